@@ -1,0 +1,406 @@
+/*
+ * srj_oracle.c -- plain, slow, FP64 CPU oracle for Scheduled Relaxation
+ * Jacobi (SRJ) with the data-driven scheme-selection heuristic of
+ * Islam & Wang, "A data driven heuristic for rapid convergence of Scheduled
+ * Relaxation Jacobi schemes" (arXiv:2011.06636).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference that the
+ * CUDA library is checked against.  It shares no code, header, table or
+ * constant generator with the library under paper_2011_06636_gb300/, and
+ * nothing in the product path may call it.  Only tests/, the smoke check and
+ * the CPU-baseline leg of bench.py load it.
+ *
+ * Everything is double precision, written for a reader to check against the
+ * paper by eye: no blocking, no fusion, no reordering beyond what the
+ * equations state.  Each function cites the passage it follows.
+ *
+ * Readings of points the paper leaves open (all listed in the design doc):
+ *  - within-cycle order of the relaxation factors: Leja order of the
+ *    Chebyshev roots, starting from the largest root (largest omega);
+ *    Sec. 2 only asks for an order that keeps roundoff under control.
+ *  - residual ratio = r_after / r_before (Sec. 3, Alg. 1 thresholds < 1).
+ *  - ratio exactly 0.4 or 0.2 keeps the level (Alg. 1 uses strict tests).
+ *  - the level is clamped to [0, 24] (App. B lists 25 levels).
+ *  - the first cycle runs at level 0; a decision follows every cycle.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_LEVEL 24
+
+/* App. B (Table "Relationship between M and scheme level"): scheme level ->
+ * number M of relaxation factors in one cycle.  Copied from the paper. */
+static const int OR_LEVEL_M[OR_MAX_LEVEL + 1] = {
+    1, 2, 3, 5, 7, 10, 14, 19, 26, 35, 47, 63, 84,
+    111, 147, 194, 256, 338, 446, 589, 778, 1027, 1356, 1790, 2362};
+
+int oracle_level_m(int level)
+{
+    if (level < 0 || level > OR_MAX_LEVEL) return -1;
+    return OR_LEVEL_M[level];
+}
+
+/* Sec. 2, Eq. (transformation): lambda* is the argument where the Chebyshev
+ * polynomial T_M equals 3.  For x >= 1, T_M(x) = cosh(M acosh x), so
+ * lambda* = cosh(acosh(3) / M). */
+double oracle_lambda_star(int M)
+{
+    return cosh(acosh(3.0) / (double)M);
+}
+
+/* Sec. 2, Eq. (srj-relaxation-parameters): omega_j = (lambda*+1) /
+ * (2 (lambda* - x_j)) with x_j = cos((2j+1) pi / (2M)), j = 0..M-1, the roots
+ * of T_M.  Output in root order (j ascending, so omega descending). */
+void oracle_scheme_root_order(int M, double *x_out, double *omega_out)
+{
+    const double ls = oracle_lambda_star(M);
+    for (int j = 0; j < M; ++j) {
+        const double xj = cos((2.0 * j + 1.0) * M_PI / (2.0 * M));
+        if (x_out) x_out[j] = xj;
+        omega_out[j] = (ls + 1.0) / (2.0 * (ls - xj));
+    }
+}
+
+/* Within-cycle order (reading of Sec. 2, last paragraph): Leja order of the
+ * roots x_j on [-1, 1].  The first point is x_0 (largest root); each next
+ * point is the unused root that maximises the product of its distances to
+ * the roots already chosen, evaluated as a sum of logarithms.  Ties go to the
+ * smaller index.  order_out receives the root indices in application order. */
+void oracle_leja_order(int M, const double *x, int *order_out)
+{
+    double *score = (double *)malloc(sizeof(double) * (size_t)M);
+    char *used = (char *)calloc((size_t)M, 1);
+    for (int j = 0; j < M; ++j) score[j] = 0.0;
+    int cur = 0;
+    for (int step = 0; step < M; ++step) {
+        if (step > 0) {
+            int best = -1;
+            for (int j = 0; j < M; ++j) {
+                if (used[j]) continue;
+                if (best < 0 || score[j] > score[best]) best = j;
+            }
+            cur = best;
+        }
+        order_out[step] = cur;
+        used[cur] = 1;
+        for (int j = 0; j < M; ++j)
+            if (!used[j]) score[j] += log(fabs(x[j] - x[cur]));
+    }
+    free(score);
+    free(used);
+}
+
+/* The relaxation factors of one scheme level, in application order. */
+int oracle_level_omegas(int level, double *omega_out)
+{
+    const int M = oracle_level_m(level);
+    if (M < 0) return -1;
+    double *x = (double *)malloc(sizeof(double) * (size_t)M);
+    double *w = (double *)malloc(sizeof(double) * (size_t)M);
+    int *ord = (int *)malloc(sizeof(int) * (size_t)M);
+    oracle_scheme_root_order(M, x, w);
+    oracle_leja_order(M, x, ord);
+    for (int i = 0; i < M; ++i) omega_out[i] = w[ord[i]];
+    free(x);
+    free(w);
+    free(ord);
+    return M;
+}
+
+/* Sec. 2, Eq. (amplification-M-scheme): G_M(lambda) =
+ * prod_i [(1 - omega_i) + omega_i lambda]. */
+double oracle_amplification(int M, const double *omega, double lambda)
+{
+    double g = 1.0;
+    for (int i = 0; i < M; ++i) g *= (1.0 - omega[i]) + omega[i] * lambda;
+    return g;
+}
+
+/* ------------------------------------------------------------------------
+ * The linear system A u = f on a structured grid.
+ *
+ * dim in {1,2,3}; n[a] interior points on axis a (x is axis 0 and varies
+ * fastest in memory); zero Dirichlet values outside the interior.
+ * Operator (Sec. 3, 1D matrix; Sec. 4.2.2/4.2.3 for 2D/3D, extended with an
+ * axis coefficient eps[a] and an optional cell coefficient k):
+ *
+ *   (A u)_p = sum_a sum_{s=-1,+1} eps[a] * kf(p, p+s e_a) / h[a]^2
+ *                                * (u_p - u_{p+s e_a})
+ *
+ * kf = 1 when k is NULL; otherwise kf is the harmonic mean
+ * 2 k_p k_q / (k_p + k_q) of the two cells sharing the face.  k is stored with
+ * one ghost layer on every axis < dim, i.e. dims (n[a]+2), x fastest.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int dim;
+    long n[3];
+    double h[3];
+    double eps[3];
+    const double *k; /* NULL or (n0+2)(n1+2)(n2+2) cell values incl. ghosts */
+} oracle_problem;
+
+static long or_npts(const oracle_problem *P)
+{
+    long t = 1;
+    for (int a = 0; a < P->dim; ++a) t *= P->n[a];
+    return t;
+}
+
+static double or_kcell(const oracle_problem *P, const long c[3])
+{
+    /* c holds interior coordinates, possibly -1 or n[a] (ghost) */
+    long kn[3], idx = 0, stride = 1;
+    for (int a = 0; a < 3; ++a) kn[a] = (a < P->dim) ? P->n[a] + 2 : 1;
+    for (int a = 0; a < 3; ++a) {
+        long ca = (a < P->dim) ? c[a] + 1 : 0;
+        idx += ca * stride;
+        stride *= kn[a];
+    }
+    return P->k[idx];
+}
+
+static double or_face(const oracle_problem *P, const long p[3], int a, int s)
+{
+    if (!P->k) return 1.0;
+    long q[3] = {p[0], p[1], p[2]};
+    q[a] += s;
+    const double kp = or_kcell(P, p), kq = or_kcell(P, q);
+    return 2.0 * kp * kq / (kp + kq);
+}
+
+/* Value of u at the neighbour of interior point p (linear index i) one step
+ * s = -1 or +1 along axis a; zero outside the interior (zero Dirichlet). */
+static double or_neighbour(const oracle_problem *P, const double *u,
+                           const long p[3], long i, int a, int s)
+{
+    long stride = 1;
+    for (int b = 0; b < a; ++b) stride *= P->n[b];
+    const long qa = p[a] + s;
+    if (qa < 0 || qa >= P->n[a]) return 0.0;
+    return u[i + s * stride];
+}
+
+/* diagonal entry D_p of A (Sec. 2, splitting A = D + L + U) */
+static double or_diag(const oracle_problem *P, const long p[3])
+{
+    double d = 0.0;
+    for (int a = 0; a < P->dim; ++a) {
+        const double c = P->eps[a] / (P->h[a] * P->h[a]);
+        d += c * (or_face(P, p, a, -1) + or_face(P, p, a, +1));
+    }
+    return d;
+}
+
+/* (A u)_p for the interior point p with linear index i */
+static double or_apply_at(const oracle_problem *P, const double *u,
+                          const long p[3], long i)
+{
+    double acc = 0.0;
+    for (int a = 0; a < P->dim; ++a) {
+        const double c = P->eps[a] / (P->h[a] * P->h[a]);
+        for (int s = -1; s <= 1; s += 2)
+            acc += c * or_face(P, p, a, s) * (u[i] - or_neighbour(P, u, p, i, a, s));
+    }
+    return acc;
+}
+
+/* Loop bounds: axes beyond dim have a single position. */
+static long or_extent(const oracle_problem *P, int a)
+{
+    return a < P->dim ? P->n[a] : 1;
+}
+
+void oracle_apply_A(const oracle_problem *P, const double *u, double *Au)
+{
+    long i = 0;
+    for (long z = 0; z < or_extent(P, 2); ++z)
+        for (long y = 0; y < or_extent(P, 1); ++y)
+            for (long x = 0; x < or_extent(P, 0); ++x, ++i) {
+                const long p[3] = {x, y, z};
+                Au[i] = or_apply_at(P, u, p, i);
+            }
+}
+
+void oracle_diagonal(const oracle_problem *P, double *D)
+{
+    long i = 0;
+    for (long z = 0; z < or_extent(P, 2); ++z)
+        for (long y = 0; y < or_extent(P, 1); ++y)
+            for (long x = 0; x < or_extent(P, 0); ++x, ++i) {
+                const long p[3] = {x, y, z};
+                D[i] = or_diag(P, p);
+            }
+}
+
+/* ||f - A u||_2 : the L2 residual norm of Sec. 3 and Eq. (relative-residual) */
+double oracle_residual_norm(const oracle_problem *P, const double *u, const double *f)
+{
+    double sum = 0.0;
+    long i = 0;
+    for (long z = 0; z < or_extent(P, 2); ++z)
+        for (long y = 0; y < or_extent(P, 1); ++y)
+            for (long x = 0; x < or_extent(P, 0); ++x, ++i) {
+                const long p[3] = {x, y, z};
+                const double r = f[i] - or_apply_at(P, u, p, i);
+                sum += r * r;
+            }
+    return sqrt(sum);
+}
+
+/* One weighted Jacobi sweep, Sec. 2, Eq. (relaxed-jacobi):
+ *   x' = omega [B_J x + D^-1 b] + (1 - omega) x,  B_J = -D^-1 (L + U),
+ * which is x' = x + omega D^-1 (b - A x).  Out of place. */
+void oracle_sweep(const oracle_problem *P, const double *u_in, const double *f,
+                  double omega, double *u_out)
+{
+    long i = 0;
+    for (long z = 0; z < or_extent(P, 2); ++z)
+        for (long y = 0; y < or_extent(P, 1); ++y)
+            for (long x = 0; x < or_extent(P, 0); ++x, ++i) {
+                const long p[3] = {x, y, z};
+                const double r = f[i] - or_apply_at(P, u_in, p, i);
+                u_out[i] = u_in[i] + omega * r / or_diag(P, p);
+            }
+}
+
+/* Apply a list of relaxation factors in order (a partial or whole cycle). */
+void oracle_sweeps(const oracle_problem *P, double *u, const double *f,
+                   const double *omega, long count)
+{
+    const long N = or_npts(P);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)N);
+    for (long s = 0; s < count; ++s) {
+        oracle_sweep(P, u, f, omega[s], tmp);
+        memcpy(u, tmp, sizeof(double) * (size_t)N);
+    }
+    free(tmp);
+}
+
+/* Sec. 3, Alg. 1 (the data-driven heuristic), with the readings listed at the
+ * top of this file.  rule 0 = heuristic, 1 = increasing (Sec. 4, the brute
+ * force comparator that raises the level every cycle), 2 = fixed level. */
+int oracle_next_level(int rule, double ratio, int level)
+{
+    if (rule == 1) return level < OR_MAX_LEVEL ? level + 1 : level;
+    if (rule == 2) return level;
+    if (ratio > 0.4) return level < OR_MAX_LEVEL ? level + 1 : level;
+    if (ratio < 0.4 && ratio > 0.2) return level > 0 ? level - 1 : level;
+    return level;
+}
+
+/* Full SRJ solve (Sec. 3 data-collection loop and Sec. 4 experiments):
+ *   r0 = ||f - A u0||; level = level0; repeat { M sweeps of the level's
+ *   scheme; rn = ||f - A u||; ratio = rn / r_prev; stop if converged;
+ *   level = Alg. 1(ratio, level) }.
+ * tol_kind 0 = relative (Eq. relative-residual), 1 = absolute L2 norm.
+ * Returns 0 converged, 1 sweep cap reached, 2 non-finite residual.
+ * Trace arrays (may be NULL) receive per-cycle level, M and rn; at most
+ * trace_cap cycles are recorded but the count returned in *cycles_out is the
+ * true one. */
+int oracle_srj_solve(const oracle_problem *P, const double *f, double *u,
+                     double tol, int tol_kind, int rule, int level0,
+                     long max_sweeps, long *sweeps_out, long *cycles_out,
+                     double *r0_out, double *rn_out, int *trace_level,
+                     double *trace_rn, long trace_cap)
+{
+    double *omega = (double *)malloc(sizeof(double) * 2362);
+    const double r0 = oracle_residual_norm(P, u, f);
+    double rprev = r0, rn = r0;
+    int level = level0;
+    long sweeps = 0, cycles = 0;
+    int status = 1;
+    if (r0_out) *r0_out = r0;
+    if (r0 == 0.0 || (tol_kind == 1 && r0 < tol)) {
+        status = 0;
+        goto done;
+    }
+    while (sweeps < max_sweeps) {
+        const int M = oracle_level_omegas(level, omega);
+        oracle_sweeps(P, u, f, omega, M);
+        sweeps += M;
+        rn = oracle_residual_norm(P, u, f);
+        if (cycles < trace_cap) {
+            if (trace_level) trace_level[cycles] = level;
+            if (trace_rn) trace_rn[cycles] = rn;
+        }
+        cycles += 1;
+        const double ratio = rn / rprev;
+        rprev = rn;
+        if (!isfinite(rn)) {
+            status = 2;
+            break;
+        }
+        if ((tol_kind == 0 ? rn / r0 : rn) < tol) {
+            status = 0;
+            break;
+        }
+        level = oracle_next_level(rule, ratio, level);
+    }
+done:
+    if (sweeps_out) *sweeps_out = sweeps;
+    if (cycles_out) *cycles_out = cycles;
+    if (rn_out) *rn_out = rn;
+    free(omega);
+    return status;
+}
+
+/* Run an explicit list of levels (no selection): for parity of cycles.
+ * rn_out[c] receives the residual norm after cycle c. */
+void oracle_srj_run_levels(const oracle_problem *P, const double *f, double *u,
+                           const int *levels, long ncycles, double *rn_out)
+{
+    double *omega = (double *)malloc(sizeof(double) * 2362);
+    for (long c = 0; c < ncycles; ++c) {
+        const int M = oracle_level_omegas(levels[c], omega);
+        oracle_sweeps(P, u, f, omega, M);
+        if (rn_out) rn_out[c] = oracle_residual_norm(P, u, f);
+    }
+    free(omega);
+}
+
+/* Plain (unrelaxed) Jacobi, Sec. 2 Eq. (jacobi): omega = 1 every sweep; the
+ * residual is tested every check_every sweeps.  Returns 0 converged, 1 cap. */
+int oracle_jacobi_solve(const oracle_problem *P, const double *f, double *u,
+                        double tol, int tol_kind, long check_every,
+                        long max_sweeps, long *sweeps_out, double *rn_out)
+{
+    const double r0 = oracle_residual_norm(P, u, f);
+    const double one = 1.0;
+    long sweeps = 0;
+    double rn = r0;
+    int status = 1;
+    if (r0 == 0.0) status = 0;
+    while (status != 0 && sweeps < max_sweeps) {
+        for (long s = 0; s < check_every; ++s) oracle_sweeps(P, u, f, &one, 1);
+        sweeps += check_every;
+        rn = oracle_residual_norm(P, u, f);
+        if ((tol_kind == 0 ? rn / r0 : rn) < tol) status = 0;
+    }
+    if (sweeps_out) *sweeps_out = sweeps;
+    if (rn_out) *rn_out = rn;
+    return status;
+}
+
+/* Thomas algorithm: direct solve of a tridiagonal system
+ *   a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i,  i = 0..N-1
+ * (a_0 and c_{N-1} unused).  Textbook forward elimination / back
+ * substitution without pivoting; valid for the diagonally dominant matrices
+ * of Sec. 3 and Sec. 4.2.1. */
+void oracle_thomas(long N, const double *a, const double *b, const double *c,
+                   const double *d, double *x)
+{
+    double *cp = (double *)malloc(sizeof(double) * (size_t)N);
+    double *dp = (double *)malloc(sizeof(double) * (size_t)N);
+    cp[0] = c[0] / b[0];
+    dp[0] = d[0] / b[0];
+    for (long i = 1; i < N; ++i) {
+        const double m = b[i] - a[i] * cp[i - 1];
+        cp[i] = (i < N - 1) ? c[i] / m : 0.0;
+        dp[i] = (d[i] - a[i] * dp[i - 1]) / m;
+    }
+    x[N - 1] = dp[N - 1];
+    for (long i = N - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+    free(cp);
+    free(dp);
+}

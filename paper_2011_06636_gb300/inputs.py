@@ -1,0 +1,111 @@
+"""Seeded synthetic inputs for the SRJ solver and its oracle.
+
+This module holds no arithmetic of the method itself: it only draws right-hand
+sides, coefficient fields and problem lists from ``numpy`` PCG64 generators
+(``default_rng(seed)``), so that the CUDA library and the FP64 oracle are fed
+identical data.  Arrays follow the library's layout: x varies fastest, so the
+numpy shape is the grid sizes reversed, ``(nz, ny, nx)``.
+
+Recipes (the paper uses no dataset; every workload is synthetic):
+
+* 1D Poisson, 16 sine modes: ``f_i = sum_m a_m sin(k_m pi i / (N+1))``,
+  i = 1..N, with 16 distinct wavenumbers k_m drawn uniformly from 1..N and
+  amplitudes a_m ~ N(0, 1).
+* 2D Poisson on a large grid: f i.i.d. uniform[-1, 1].
+* 3D variable-coefficient diffusion: log k is a Gaussian random field with
+  covariance exp(-r^2 / (2 L^2)), L = 16 cells, sigma = 1: white noise
+  convolved along each axis with a Gaussian of standard deviation L/sqrt(2)
+  cells (truncated at 4 standard deviations, reflecting edges), rescaled to
+  zero mean and unit variance, times sigma.  k = exp(log k) is drawn on the
+  interior plus one ghost layer per axis.  f i.i.d. N(0, 1).
+* Batched mixed sizes: square 2D grids with sides uniform in [64, 1024]; half
+  of the problems (chosen at random) are the constant-coefficient Laplacian,
+  the others the anisotropic operator -eps u_xx - u_yy with eps log-uniform in
+  [1e-2, 1]; f i.i.d. N(0, 1).
+* The paper's own experiments: b = 1 (Sec. 3, Sec. 4.1) and f = 1 (Sec. 4.2.3).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def shape_of(n):
+    """numpy shape of a grid whose interior sizes are ``n`` (x first)."""
+    return tuple(int(v) for v in reversed(list(n)))
+
+
+def poisson1d_sines(N: int, seed: int, modes: int = 16) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    ks = rng.choice(np.arange(1, N + 1), size=min(modes, N), replace=False)
+    amps = rng.standard_normal(len(ks))
+    i = np.arange(1, N + 1, dtype=np.float64)
+    f = np.zeros(N)
+    for a, k in zip(amps, ks):
+        f += a * np.sin(k * math.pi * i / (N + 1))
+    return f
+
+
+def uniform_rhs(n, seed: int, lo: float = -1.0, hi: float = 1.0,
+                dtype=np.float64) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=shape_of(n)).astype(dtype)
+
+
+def normal_rhs(n, seed: int, dtype=np.float64) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(size=shape_of(n)).astype(dtype)
+
+
+def ones_rhs(n, dtype=np.float64) -> np.ndarray:
+    return np.ones(shape_of(n), dtype=dtype)
+
+
+def _gauss_kernel(std: float):
+    r = int(math.ceil(4.0 * std))
+    t = np.arange(-r, r + 1, dtype=np.float64)
+    g = np.exp(-0.5 * (t / std) ** 2)
+    return g / g.sum()
+
+
+def _conv_axis_reflect(a: np.ndarray, g: np.ndarray, axis: int) -> np.ndarray:
+    r = (len(g) - 1) // 2
+    pad = [(0, 0)] * a.ndim
+    pad[axis] = (r, r)
+    p = np.pad(a, pad, mode="symmetric")
+    out = np.zeros_like(a)
+    n = a.shape[axis]
+    for t, w in enumerate(g):
+        sl = [slice(None)] * a.ndim
+        sl[axis] = slice(t, t + n)
+        out += w * p[tuple(sl)]
+    return out
+
+
+def lognormal_k(n, seed: int, corr: float = 16.0, sigma: float = 1.0,
+                dtype=np.float64) -> np.ndarray:
+    """Cell coefficient k with one ghost layer: numpy shape (n[::-1] + 2)."""
+    rng = np.random.default_rng(seed)
+    shp = tuple(v + 2 for v in shape_of(n))
+    g = rng.standard_normal(size=shp)
+    ker = _gauss_kernel(corr / math.sqrt(2.0))
+    for ax in range(g.ndim):
+        g = _conv_axis_reflect(g, ker, ax)
+    g = (g - g.mean()) / g.std()
+    return np.exp(sigma * g).astype(dtype)
+
+
+def batched_problems(count: int = 256, seed: int = 0, smin: int = 64,
+                     smax: int = 1024):
+    """List of dicts {n: [side, side], eps: [eps_x, 1.0], seed_f: int}."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(smin, smax + 1, size=count)
+    aniso = rng.permutation(count) < count // 2
+    logeps = rng.uniform(math.log(1e-2), math.log(1.0), size=count)
+    out = []
+    for i in range(count):
+        e = math.exp(logeps[i]) if aniso[i] else 1.0
+        out.append(dict(n=[int(sides[i]), int(sides[i])], eps=[e, 1.0],
+                        seed_f=int(seed * 100003 + i)))
+    return out
