@@ -1,0 +1,333 @@
+"""Benchmark: one step = one SRJ solve of the 2D Poisson problem on a
+4096 x 4096 interior grid (5-point stencil, zero Dirichlet, f i.i.d.
+uniform[-1, 1] seed 0, u0 = 0) to relative residual 1e-8, with the paper's
+scheme family and Alg. 1 selection, through the library's C ABI.
+
+The timed solve is the mixed-precision path (FP64 refinement around
+FP32-arithmetic inner SRJ on an FP32-pair iterate); the plain FP64 SRJ solve
+of the same problem is timed once afterwards for the mixed-vs-plain ratio.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (the
+solve does not shard across GPUs here): each rank solves its own seeded
+problem, value = all ranks' grid-point updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("GLUP/s (% HBM roofline) and time to 1e-8 rel. residual, learned/mixed vs plain SRJ")
+UNIT = "GLUP/s"
+SIDE = 4096
+TOL = 1e-8
+WORKLOAD = ("2D Poisson 5-point, 4096x4096 interior, zero Dirichlet, f~U[-1,1] (seed 0+rank), "
+            "u0=0, rel residual 1e-8, SRJ scheme family + Alg. 1 heuristic")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(smax)
+            out["samples"] = len(sm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("SRJ_BENCH_GLOO") is None else "gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(world, v):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- oracle arm
+def oracle_sample(seconds_budget=15.0):
+    """Time the FP64 oracle's sweeps on the same 4096^2 problem: whole cycles
+    at levels 0, 1, 2, ... until the budget is used.  Returns (GLUP/s, text)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2011_06636_gb300 import inputs
+    n = [SIDE, SIDE]
+    f = inputs.uniform_rhs(n, seed=0).ravel()
+    P = O.Problem(n)
+    u = np.zeros(f.size)
+    t0 = time.perf_counter()
+    sweeps, level = 0, 0
+    while True:
+        w = O.level_omegas(level)
+        u = O.sweeps(P, u, f, w)
+        sweeps += len(w)
+        level += 1
+        if time.perf_counter() - t0 > seconds_budget:
+            break
+    dt = time.perf_counter() - t0
+    return sweeps * f.size / dt / 1e9, dt, "%d sweeps (cycles at levels 0..%d) of the 4096^2 problem" % (
+        sweeps, level - 1)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    budget = float(os.environ.get("SRJ_ORACLE_STEP_SECONDS", "6"))
+    for _ in range(args.warmup):
+        oracle_sample(budget / 4)
+    vals, times, sample = [], [], ""
+    for _ in range(args.steps):
+        v, dt, sample = oracle_sample(budget)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [SIDE, SIDE]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step: " + sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2011_06636_gb300 import _build, inputs, srj
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    _build.build()
+    srj.load(build_if_missing=False)
+    n = [SIDE, SIDE]
+    npts = SIDE * SIDE
+    f_np = inputs.uniform_rhs(n, seed=rank).ravel()
+    stream = torch.cuda.current_stream()
+    f = torch.as_tensor(f_np, device="cuda")
+    u = torch.zeros(npts, dtype=torch.float64, device="cuda")
+    h = srj.srj_create(n, precision=srj.SRJ_PREC_MIXED, stream=stream.cuda_stream)
+
+    def step():
+        u.zero_()
+        return srj.srj_solve(h, f.data_ptr(), u.data_ptr(), TOL)
+
+    for _ in range(args.warmup):
+        st = step()
+    torch.cuda.synchronize()
+    barrier(world)
+    stats = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            stats.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = allmax(world, ms)
+    sweeps = sum(s["sweeps"] for s in stats)
+    passes = sum(s["passes"] for s in stats)
+    outer = sum(s["outer"] for s in stats)
+    lups = allsum(world, float(sweeps) * npts)
+    value = lups / (ms_max * 1e-3) / 1e9
+    ok = all(s["status"] == srj.SRJ_OK for s in stats)
+    # relative residual of the last solve, checked independently in FP64 torch
+    uu = u.view(SIDE, SIDE)
+    ff = f.view(SIDE, SIDE)
+    up = torch.nn.functional.pad(uu, (1, 1, 1, 1))
+    hinv2 = float((SIDE + 1) ** 2)
+    Au = hinv2 * (4 * uu - up[1:-1, :-2] - up[1:-1, 2:] - up[:-2, 1:-1] - up[2:, 1:-1])
+    rel_check = float(torch.linalg.norm(ff - Au) / torch.linalg.norm(ff))
+
+    # dominant kernel: inner pass; per-pass device time over the timed region
+    pass_ms = ms / max(passes, 1)
+    bytes_per_pass = 20.0 * npts  # FP32-pair iterate read+write (8+8) + FP32 rhs (4)
+    hbm_peak, peak_kind = peaks()
+    achieved = bytes_per_pass / (pass_ms * 1e-3) / 1e9
+
+    # end to end through srj_solve_host with pinned host buffers
+    fh = torch.as_tensor(f_np).pin_memory()
+    uh = torch.zeros(npts, dtype=torch.float64).pin_memory()
+    e2e_st = srj.srj_solve_host(h, fh.data_ptr(), uh.data_ptr(), TOL)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_sweeps = 0
+    for _ in range(args.steps):
+        uh.zero_()
+        e2e_st = srj.srj_solve_host(h, fh.data_ptr(), uh.data_ptr(), TOL)
+        e2e_sweeps += e2e_st["sweeps"]
+    e2e_s = allmax(world, time.perf_counter() - t0)
+    e2e_val = allsum(world, float(e2e_sweeps) * npts) / e2e_s / 1e9
+    srj.srj_destroy(h)
+
+    # plain FP64 SRJ with the heuristic on the same problem (comparator)
+    fp64 = None
+    if not args.no_fp64:
+        h64 = srj.srj_create(n, precision=srj.SRJ_PREC_F64, stream=stream.cuda_stream)
+        u.zero_()
+        s64 = srj.srj_solve(h64, f.data_ptr(), u.data_ptr(), TOL)
+        srj.srj_destroy(h64)
+        fp64 = {"time_to_tol_s": s64["seconds"], "sweeps": s64["sweeps"],
+                "glups": s64["sweeps"] * npts / s64["seconds"] / 1e9,
+                "status": srj.STATUS_NAMES[s64["status"]]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, sample = oracle_sample(float(os.environ.get("SRJ_ORACLE_SECONDS", "15")))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 sweeps on an FP32-pair iterate; f64 outer residual/update",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [SIDE, SIDE],
+                       "precision": "mixed (FP64 refinement, FP32-pair inner)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (u+f FP64 268 MB, inner working set 335 MB)"},
+            "time_to_tol_s": ms_max / args.steps / 1e3,
+            "sweeps_per_solve": sweeps / args.steps, "outer_per_solve": outer / args.steps,
+            "converged": ok, "rel_residual_check": rel_check,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "inner pass (FP32-pair iterate), per-pass device time over "
+                                   "the timed region", "peak_kind": peak_kind},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * npts,
+                    "d2h_bytes_per_step": 8 * npts},
+            "gpu_launches": int(passes + 2 * outer + args.steps),
+            "plain_fp64": fp64,
+            "mixed_vs_plain_speedup": (fp64["time_to_tol_s"] / (ms_max / args.steps / 1e3))
+            if fp64 else None,
+            "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, world = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    rank, world = dist_init()
+    run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

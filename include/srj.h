@@ -1,0 +1,189 @@
+/*
+ * srj.h -- C ABI of libsrj.so: a GB300 (sm_103a) solver for the linear
+ * system A u = f on structured grids by Scheduled Relaxation Jacobi (SRJ)
+ * with the data-driven per-cycle scheme selection of Islam & Wang,
+ * "A data driven heuristic for rapid convergence of Scheduled Relaxation
+ * Jacobi schemes" (arXiv:2011.06636).
+ *
+ * The operator (Sec. 3 1D matrix, Sec. 4.2 2D/3D finite differences,
+ * generalised with per-axis and per-cell coefficients):
+ *
+ *   (A u)_p = sum_a sum_{s=-1,+1} eps_a * kf(p, p + s e_a) / h_a^2
+ *                                     * (u_p - u_{p + s e_a})
+ *
+ * on dim = 1, 2 or 3 axes with zero Dirichlet values outside the interior.
+ * kf = 1 for constant coefficients, else the harmonic mean
+ * 2 k_p k_q / (k_p + k_q) of the cell coefficients on both sides of a face.
+ *
+ * One SRJ cycle at scheme level L applies the M = M(L) relaxation factors of
+ * App. B / Sec. 2 Eq. (srj-relaxation-parameters) as weighted Jacobi sweeps
+ * u <- u + omega D^-1 (f - A u) (Sec. 2, Eq. relaxed-jacobi), then takes the
+ * L2 residual norm ||f - A u|| and picks the next level by Sec. 3, Alg. 1.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are dense, interior points only, x fastest:
+ *    index = x + n0 * (y + n1 * z).
+ *  - Pointers documented as DEVICE must be CUDA device (or managed) memory
+ *    of the current device; HOST pointers are ordinary host memory.
+ *  - The caller owns every array it passes; the library never frees them and
+ *    keeps no reference to f, u or k after the call returns.  The library
+ *    owns its workspace (internal padded copies, scheme tables, reduction
+ *    scratch, per-cycle trace, CUDA graphs), released by srj_destroy.
+ *  - Errors are returned as srj_status codes; no entry point throws, traps
+ *    or aborts.  srj_last_error() gives a text for the last failure on a
+ *    handle.  A handle is not thread safe; distinct handles are independent.
+ *  - Work is queued on the stream given at creation (NULL = legacy default
+ *    stream).  srj_solve*, srj_run_levels, srj_residual_norm synchronise
+ *    that stream before returning (they return host-side results).
+ */
+#ifndef SRJ_H
+#define SRJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srj_handle srj_handle;
+
+typedef enum srj_status {
+    SRJ_OK = 0,
+    SRJ_EINVAL = 1,       /* invalid argument (null pointer, size, option) */
+    SRJ_ENOMEM = 2,       /* device or host allocation failed */
+    SRJ_ECUDA = 3,        /* a CUDA runtime call failed (see srj_last_error) */
+    SRJ_ENOTCONV = 4,     /* sweep cap reached before the tolerance */
+    SRJ_EDIVERGED = 5,    /* the residual norm became non-finite */
+    SRJ_ETIMEOUT = 6,     /* reserved: a bounded device-side wait expired */
+    SRJ_EUNSUPPORTED = 7  /* valid request the library does not implement */
+} srj_status;
+
+/* Per-cycle level selection. */
+enum srj_selector {
+    SRJ_SEL_HEURISTIC = 0,  /* Sec. 3, Alg. 1: ratio > 0.4 up, 0.2 < ratio < 0.4 down */
+    SRJ_SEL_INCREASING = 1, /* Sec. 4: raise the level every cycle */
+    SRJ_SEL_FIXED = 2,      /* stay at opts.fixed_level */
+    SRJ_SEL_MLP = 3         /* learned selector (srj_mlp_set_weights), Alg. 1 as fallback */
+};
+
+/* Arithmetic of the sweeps; f and u element types follow it. */
+enum srj_precision {
+    SRJ_PREC_F64 = 0,   /* FP64 sweeps; f, u are double */
+    SRJ_PREC_F32 = 1,   /* FP32 sweeps; f, u are float (roundoff floor ~ kappa*eps32) */
+    SRJ_PREC_MIXED = 2  /* FP64 iterative refinement (r = f - A u, u += e in FP64)
+                           around FP32-arithmetic inner SRJ on A e = r whose iterate
+                           is kept as an unevaluated pair of FP32 values; f, u double */
+};
+
+enum srj_tol_kind {
+    SRJ_TOL_REL = 0,  /* ||f - A u|| / ||f - A u0|| < tol (Sec. 4.2.3, Eq. relative-residual) */
+    SRJ_TOL_ABS = 1   /* ||f - A u|| < tol (Sec. 4.1) */
+};
+
+typedef struct srj_grid {
+    int32_t dim;   /* 1, 2 or 3 */
+    int64_t n[3];  /* interior points per axis, x first; axes >= dim ignored */
+    double h[3];   /* grid spacing per axis; 0 means 1/(n+1) (unit domain) */
+} srj_grid;
+
+typedef struct srj_stencil {
+    double eps[3];   /* axis coefficients; 0 means 1 (Poisson) */
+    const double *k; /* NULL: constant coefficients.  Else a DEVICE array of the
+                        cell coefficient including one ghost layer per axis:
+                        (n0+2)(n1+2)(n2+2) doubles (axes >= dim count 1), x
+                        fastest, all entries finite and > 0.  Read only during
+                        srj_create (face coefficients are derived there). */
+} srj_stencil;
+
+typedef struct srj_opts {
+    int32_t selector;       /* enum srj_selector */
+    int32_t precision;      /* enum srj_precision */
+    int32_t tol_kind;       /* enum srj_tol_kind */
+    int32_t level0;         /* level of the first cycle (Sec. 3 uses 0) */
+    int32_t fixed_level;    /* level for SRJ_SEL_FIXED */
+    int32_t max_level;      /* highest selectable level, <= 24 (0 means 24) */
+    int32_t temporal_depth; /* sweeps fused per HBM pass; 0 = library choice */
+    int32_t trace_capacity; /* per-cycle records kept (0 means 4096) */
+    int64_t max_sweeps;     /* sweep cap per solve (0 means 1000000) */
+    double inner_tol;       /* SRJ_PREC_MIXED: inner relative tolerance (0 means 1e-4) */
+} srj_opts;
+
+typedef struct srj_stats {
+    int32_t status;      /* srj_status of the solve */
+    int32_t final_level; /* level of the last cycle run */
+    int64_t sweeps;      /* relaxed Jacobi sweeps = the paper's iterations */
+    int64_t cycles;      /* SRJ cycles (for MIXED: summed over inner solves) */
+    int64_t outer;       /* MIXED: refinement steps; otherwise 0 */
+    int64_t passes;      /* kernel passes over the grid */
+    double r0;           /* ||f - A u0||_2 */
+    double rn;           /* ||f - A u||_2 at exit (FP64 for F64 and MIXED) */
+    double seconds;      /* device time of the solve, CUDA events */
+} srj_stats;
+
+/* Library version string (static storage). */
+const char *srj_version(void);
+
+/* App. B: number of relaxation factors M of a scheme level, or -1 if the
+ * level is outside [0, 24]. */
+int32_t srj_level_m(int32_t level);
+
+/* Sec. 2, Eq. (srj-relaxation-parameters): writes the M(level) relaxation
+ * factors of a level into the HOST array omega_out (capacity entries), in the
+ * order the library applies them within a cycle (Leja order of the Chebyshev
+ * roots, largest factor first).  Returns M, or -1 for a bad level or a too
+ * small capacity. */
+int32_t srj_scheme_omegas(int32_t level, double *omega_out, int32_t capacity);
+
+/* Create a solver for one grid.  grid, stencil and opts are HOST structs
+ * (stencil may be NULL: Poisson; opts may be NULL: defaults).  stream is a
+ * cudaStream_t (NULL = legacy default stream).  Allocates the device
+ * workspace (about 3-6 arrays of the grid size) and the scheme tables on the
+ * current device.  On failure *out is NULL and the status says why. */
+srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil,
+                      const srj_opts *opts, void *stream, srj_handle **out);
+
+/* Solve A u = f to tol (kind from opts).  f and u are DEVICE arrays of the
+ * grid size with the element type of the precision (double for F64 and
+ * MIXED, float for F32); u holds u0 on entry and the result on exit.
+ * stats (HOST, may be NULL) receives the counters.  Returns SRJ_OK when
+ * converged, SRJ_ENOTCONV / SRJ_EDIVERGED otherwise (u then holds the last
+ * iterate). */
+srj_status srj_solve(srj_handle *h, const void *f, void *u, double tol,
+                     srj_stats *stats);
+
+/* As srj_solve, but f and u are HOST arrays: the host-to-device copies of f
+ * and u0 and the device-to-host copy of u are part of the call (and of
+ * stats->seconds).  Pinned host memory gives the fastest copies. */
+srj_status srj_solve_host(srj_handle *h, const void *f_host, void *u_host,
+                          double tol, srj_stats *stats);
+
+/* Run an explicit list of ncycles levels (HOST array) without selection and
+ * without a convergence test: for each entry one whole cycle of M(level)
+ * sweeps.  f, u as for srj_solve.  rn_out (HOST, ncycles doubles, may be
+ * NULL) receives ||f - A u|| after each cycle.  Precision F64 or F32 only. */
+srj_status srj_run_levels(srj_handle *h, const void *f, void *u,
+                          const int32_t *levels, int64_t ncycles,
+                          double *rn_out);
+
+/* ||f - A u||_2 of DEVICE arrays f, u (types as for srj_solve), into *out. */
+srj_status srj_residual_norm(srj_handle *h, const void *f, const void *u,
+                             double *out);
+
+/* Copy the per-cycle record of the last solve (level and ||f - A u|| after
+ * each cycle; for MIXED the inner cycles, rn relative to that inner solve's
+ * right-hand side) into HOST arrays of the given capacity.  Returns the
+ * number of cycles of the last solve (may exceed capacity) or -1. */
+int64_t srj_get_trace(const srj_handle *h, int32_t *levels, double *rn,
+                      int64_t capacity);
+
+/* Text describing the last failure on h (static storage inside h), or a
+ * generic text for h == NULL. */
+const char *srj_last_error(const srj_handle *h);
+
+/* Release the handle and all library-owned device memory and graphs. */
+srj_status srj_destroy(srj_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SRJ_H */

@@ -1,0 +1,609 @@
+// api.cu -- the extern "C" entry points of libsrj.so (declared in
+// include/srj.h) and the host-side orchestration:
+//
+//  * srj_create derives the geometry, uploads the scheme tables (Sec. 2,
+//    App. B) and allocates the workspace.
+//  * One SRJ solve is one launch of a CUDA graph made of a conditional WHILE
+//    node whose body is a single pass kernel.  The pass kernels update a
+//    device-resident state (cycle position, residual history, level chosen by
+//    Alg. 1) and the last CTA of the final pass clears the loop condition, so
+//    a whole solve -- thousands of passes -- runs without the host.
+//  * SRJ_PREC_MIXED runs FP64 iterative refinement on the host side around
+//    that graph: FP64 r = f - A u, inner SRJ on A e = r with FP32 arithmetic
+//    on an FP32-pair iterate, FP64 u += e.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "srj_internal.h"
+
+using namespace srj;
+
+struct srj_handle {
+    GridGeo geo{};
+    int user_prec = SRJ_PREC_F64;  // srj_precision
+    int kprec = PREC_F64;          // precision of the pass kernels
+    bool vark = false;
+    srj_opts opts{};
+    cudaStream_t stream = nullptr;
+    long long npts = 0;    // dense interior points
+    long long padded = 0;  // padded elements (plane * nz)
+    size_t esize = 8;      // user element size
+
+    // scheme tables
+    double *w64 = nullptr;
+    float *w32 = nullptr;
+    // iterate buffers (padded).  F64/F32: F, U[2].  MIXED: R32 (as F), E hi/lo.
+    void *F = nullptr;
+    void *U[2] = {nullptr, nullptr};
+    void *Ulo[2] = {nullptr, nullptr};
+    // variable coefficients
+    double *wx64 = nullptr, *wy64 = nullptr, *wz64 = nullptr, *invd64 = nullptr;
+    float *wx32 = nullptr, *wy32 = nullptr, *wz32 = nullptr, *invd32 = nullptr;
+    // state, reductions, trace, schedule
+    DevState *st = nullptr;
+    DevState *h_st = nullptr;  // pinned
+    double *partials = nullptr;
+    int partials_cap = 0;
+    int32_t *trace_level = nullptr;
+    double *trace_rn = nullptr;
+    int trace_cap = 0;
+    int32_t *sched = nullptr;
+    // mixed-precision outer
+    double *opartials = nullptr;
+    unsigned int *oticket = nullptr;
+    double *onorm2 = nullptr;
+    double *h_onorm2 = nullptr;  // pinned
+    // dense device staging for srj_solve_host
+    void *dF = nullptr, *dU = nullptr;
+    // graph of the device-driven cycle loop
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    long long last_cycles = 0;
+    std::string err;
+};
+
+namespace {
+
+const char *kVersion = "srj-gb300 0.1 (sm_103a)";
+
+srj_status fail(srj_handle *h, srj_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                    \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return fail(h, SRJ_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    return cudaMalloc((void **)p, bytes);
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+PassLaunch make_launch(srj_handle *h, bool inner) {
+    PassLaunch a{};
+    a.geo = h->geo;
+    a.bufs.f = h->F;
+    a.bufs.u[0] = h->U[0];
+    a.bufs.u[1] = h->U[1];
+    a.bufs.ulo[0] = h->Ulo[0];
+    a.bufs.ulo[1] = h->Ulo[1];
+    if (h->vark) {
+        const bool f64 = h->kprec == PREC_F64;
+        a.bufs.wx = f64 ? (const void *)h->wx64 : (const void *)h->wx32;
+        a.bufs.wy = f64 ? (const void *)h->wy64 : (const void *)h->wy32;
+        a.bufs.wz = f64 ? (const void *)h->wz64 : (const void *)h->wz32;
+        a.bufs.invd = f64 ? (const void *)h->invd64 : (const void *)h->invd32;
+    }
+    (void)inner;
+    a.st = h->st;
+    a.partials = h->partials;
+    a.partials_cap = h->partials_cap;
+    a.w64 = h->w64;
+    a.w32 = h->w32;
+    a.cfg.sched = h->sched;
+    a.cfg.trace_level = h->trace_level;
+    a.cfg.trace_rn = h->trace_rn;
+    a.cfg.trace_cap = h->trace_cap;
+    a.cfg.use_cond = 0;
+    a.cfg.mlp_w = nullptr;
+    for (int l = 0; l < kNumLevels; ++l) {
+        a.lvl_m[l] = kLevelM[l];
+        a.lvl_off[l] = level_offset(l);
+    }
+    return a;
+}
+
+// Graph: WHILE(cond) { pass kernel }.  Built once per handle.
+srj_status build_graph(srj_handle *h) {
+    if (h->exec) return SRJ_OK;
+    CK(cudaGraphCreate(&h->graph, 0));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, h->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    PassLaunch a = make_launch(h, true);
+    a.cfg.use_cond = 1;
+    a.cfg.cond = cond;
+    CK(add_generic_pass_node(h->kprec, h->vark, a, body));
+    CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+    return SRJ_OK;
+}
+
+void init_state(srj_handle *h, DevState &s, double tol, int tol_kind, int selector,
+                int level0, long long max_sweeps, int stall_stop, int nsched, int trace_base) {
+    std::memset(&s, 0, sizeof(s));
+    s.tol = tol;
+    s.tol_kind = tol_kind;
+    s.selector = selector;
+    s.fixed_level = h->opts.fixed_level;
+    s.max_level = h->opts.max_level;
+    s.max_sweeps = max_sweeps;
+    s.stall_stop = stall_stop;
+    s.nsched = nsched;
+    s.level = level0;
+    s.trace_base = trace_base;
+    s.status = DST_RUNNING;
+}
+
+srj_status status_of(int dst) {
+    switch (dst) {
+        case DST_CONVERGED:
+        case DST_DONE:
+            return SRJ_OK;
+        case DST_DIVERGED:
+            return SRJ_EDIVERGED;
+        default:
+            return SRJ_ENOTCONV;
+    }
+}
+
+// Plain F64 / F32 solve on DEVICE dense arrays (timed by the caller's events).
+srj_status solve_plain(srj_handle *h, const void *f, void *u, double tol, int selector,
+                       int level0, int nsched, srj_stats *stats) {
+    srj_status s = build_graph(h);
+    if (s != SRJ_OK) return s;
+    cudaStream_t st = h->stream;
+    CK(copy_in_launch(h->kprec, h->geo, f, h->F, st));
+    CK(copy_in_launch(h->kprec, h->geo, u, h->U[0], st));
+    init_state(h, *h->h_st, tol, h->opts.tol_kind, selector, level0, h->opts.max_sweeps, 0,
+               nsched, 0);
+    CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
+    CK(cudaGraphLaunch(h->exec, st));
+    void *pads[2] = {h->U[0], h->U[1]};
+    CK(copy_out_launch(h->kprec, h->geo, h->st, pads, u, st));
+    CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const DevState &r = *h->h_st;
+    h->last_cycles = r.cycles;
+    if (stats) {
+        stats->status = status_of(r.status);
+        stats->final_level = r.level;
+        stats->sweeps = r.sweeps;
+        stats->cycles = r.cycles;
+        stats->outer = 0;
+        stats->passes = r.passes;
+        stats->r0 = r.r0;
+        stats->rn = r.rn;
+    }
+    return status_of(r.status);
+}
+
+// FP64 iterative refinement around FP32-arithmetic inner SRJ solves.
+srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, srj_stats *stats) {
+    srj_status s = build_graph(h);
+    if (s != SRJ_OK) return s;
+    cudaStream_t st = h->stream;
+    OuterArgs oa{};
+    oa.geo = h->geo;
+    oa.f = f;
+    oa.u = u;
+    oa.u_out = u;
+    oa.r32 = (float *)h->F;
+    oa.ehi[0] = (const float *)h->U[0];
+    oa.ehi[1] = (const float *)h->U[1];
+    oa.elo[0] = (const float *)h->Ulo[0];
+    oa.elo[1] = (const float *)h->Ulo[1];
+    oa.inner = h->st;
+    oa.wx = h->wx64;
+    oa.wy = h->wy64;
+    oa.wz = h->wz64;
+    oa.invd = h->invd64;
+    oa.partials = h->opartials;
+    oa.ticket = h->oticket;
+    oa.out_norm2 = h->onorm2;
+
+    const int kCarry = 3;  // inner solves restart this many levels below the last one
+    const long long kInnerCap = 200000;  // sweeps of one inner solve
+    const long long max_sweeps = h->opts.max_sweeps;
+    long long sweeps = 0, cycles = 0, passes = 0, outer = 0;
+    double r0 = 0.0, rn = 0.0;
+    int level = h->opts.level0, final_level = level;
+    int result = DST_NOTCONV;
+    int trace_base = 0;
+    const size_t ebytes = (size_t)h->padded * sizeof(float);
+    for (;;) {
+        CK(outer_residual_launch(oa, st));
+        CK(cudaMemcpyAsync(h->h_onorm2, h->onorm2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (outer > 0) {  // fold in the inner solve that just finished
+            const DevState &r = *h->h_st;
+            sweeps += r.sweeps;
+            cycles += r.cycles;
+            passes += r.passes;
+            final_level = r.level;
+            level = r.level - kCarry > 0 ? r.level - kCarry : 0;
+            trace_base += (int)r.cycles;
+            if (r.status == DST_DIVERGED) {
+                result = DST_DIVERGED;
+                break;
+            }
+        }
+        rn = std::sqrt(*h->h_onorm2);
+        if (outer == 0) r0 = rn;
+        if (!std::isfinite(rn)) {
+            result = DST_DIVERGED;
+            break;
+        }
+        const double test = h->opts.tol_kind == SRJ_TOL_ABS ? rn : (r0 > 0 ? rn / r0 : 0.0);
+        if (rn == 0.0 || test < tol) {
+            result = DST_CONVERGED;
+            break;
+        }
+        if (sweeps >= max_sweeps || outer >= 200) {
+            result = DST_NOTCONV;
+            break;
+        }
+        CK(cudaMemsetAsync(h->U[0], 0, ebytes, st));
+        CK(cudaMemsetAsync(h->Ulo[0], 0, ebytes, st));
+        const long long inner_cap = max_sweeps - sweeps < kInnerCap ? max_sweeps - sweeps
+                                                                    : kInnerCap;
+        init_state(h, *h->h_st, h->opts.inner_tol, SRJ_TOL_REL, h->opts.selector, level,
+                   inner_cap, 1, 0, trace_base);
+        CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
+        CK(cudaGraphLaunch(h->exec, st));
+        CK(outer_update_launch(oa, st));
+        CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+        outer += 1;
+    }
+    h->last_cycles = cycles;
+    if (stats) {
+        stats->status = status_of(result);
+        stats->final_level = final_level;
+        stats->sweeps = sweeps;
+        stats->cycles = cycles;
+        stats->outer = outer;
+        stats->passes = passes;
+        stats->r0 = r0;
+        stats->rn = rn;
+    }
+    return status_of(result);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *srj_version(void) { return kVersion; }
+
+int32_t srj_level_m(int32_t level) {
+    if (level < 0 || level > kMaxLevel) return -1;
+    return kLevelM[level];
+}
+
+int32_t srj_scheme_omegas(int32_t level, double *omega_out, int32_t capacity) {
+    return scheme_omegas(level, omega_out, capacity);
+}
+
+srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const srj_opts *opts,
+                      void *stream, srj_handle **out) {
+    srj_handle *h = nullptr;
+    if (out) *out = nullptr;
+    if (!grid || !out) return SRJ_EINVAL;
+    if (grid->dim < 1 || grid->dim > 3) return SRJ_EINVAL;
+    for (int a = 0; a < grid->dim; ++a)
+        if (grid->n[a] < 1 || grid->n[a] > (1LL << 30) || grid->h[a] < 0 ||
+            !std::isfinite(grid->h[a]))
+            return SRJ_EINVAL;
+    h = new (std::nothrow) srj_handle();
+    if (!h) return SRJ_ENOMEM;
+    srj_opts o{};
+    if (opts) o = *opts;
+    if (o.max_level == 0) o.max_level = kMaxLevel;
+    if (o.trace_capacity == 0) o.trace_capacity = 4096;
+    if (o.max_sweeps == 0) o.max_sweeps = 1000000LL;
+    if (o.inner_tol == 0) o.inner_tol = 1e-4;
+    auto bad = [&](const char *m) {
+        delete h;
+        (void)m;
+        return SRJ_EINVAL;
+    };
+    if (o.selector < 0 || o.selector > SRJ_SEL_MLP) return bad("selector");
+    if (o.selector == SRJ_SEL_MLP) {
+        delete h;
+        return SRJ_EUNSUPPORTED;
+    }
+    if (o.precision < 0 || o.precision > SRJ_PREC_MIXED) return bad("precision");
+    if (o.tol_kind != SRJ_TOL_REL && o.tol_kind != SRJ_TOL_ABS) return bad("tol_kind");
+    if (o.max_level < 0 || o.max_level > kMaxLevel) return bad("max_level");
+    if (o.level0 < 0 || o.level0 > o.max_level) return bad("level0");
+    if (o.fixed_level < 0 || o.fixed_level > o.max_level) return bad("fixed_level");
+    if (o.trace_capacity < 0 || o.max_sweeps < 0 || o.inner_tol < 0 || o.temporal_depth < 0)
+        return bad("negative option");
+    h->opts = o;
+    h->stream = (cudaStream_t)stream;
+    h->user_prec = o.precision;
+    h->kprec = o.precision == SRJ_PREC_F64 ? PREC_F64
+                                            : (o.precision == SRJ_PREC_F32 ? PREC_F32 : PREC_DF);
+    h->esize = o.precision == SRJ_PREC_F32 ? 4 : 8;
+
+    GridGeo &g = h->geo;
+    g.dim = grid->dim;
+    g.nx = (int)grid->n[0];
+    g.ny = grid->dim > 1 ? (int)grid->n[1] : 1;
+    g.nz = grid->dim > 2 ? (int)grid->n[2] : 1;
+    double hh[3], ee[3];
+    for (int a = 0; a < 3; ++a) {
+        const long long na = a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
+        hh[a] = (a < grid->dim && grid->h[a] > 0) ? grid->h[a] : 1.0 / (double)(na + 1);
+        const double e = stencil ? stencil->eps[a] : 0.0;
+        if (e < 0 || !std::isfinite(e)) return bad("eps");
+        ee[a] = e > 0 ? e : 1.0;
+    }
+    g.cx = ee[0] / (hh[0] * hh[0]);
+    g.cy = g.dim > 1 ? ee[1] / (hh[1] * hh[1]) : 0.0;
+    g.cz = g.dim > 2 ? ee[2] / (hh[2] * hh[2]) : 0.0;
+    g.diag = 2.0 * (g.cx + g.cy + g.cz);
+    g.pitch = ((long long)g.nx + 31) / 32 * 32;
+    g.plane = g.pitch * g.ny;
+    h->npts = (long long)g.nx * g.ny * g.nz;
+    h->padded = g.plane * g.nz;
+    h->vark = stencil && stencil->k;
+
+    // scheme tables
+    std::vector<double> w(kTotalOmegas);
+    build_omega_table(w.data());
+    std::vector<float> wf(kTotalOmegas);
+    for (int i = 0; i < kTotalOmegas; ++i) wf[i] = (float)w[i];
+#define ALLOC(ptr, bytes)                                      \
+    do {                                                       \
+        if (dalloc(&(ptr), (bytes)) != cudaSuccess) {          \
+            srj_destroy(h);                                    \
+            return SRJ_ENOMEM;                                 \
+        }                                                      \
+    } while (0)
+    ALLOC(h->w64, kTotalOmegas * sizeof(double));
+    ALLOC(h->w32, kTotalOmegas * sizeof(float));
+    const size_t kb = h->kprec == PREC_F64 ? 8 : 4;
+    ALLOC(h->F, h->padded * kb);
+    ALLOC(h->U[0], h->padded * kb);
+    ALLOC(h->U[1], h->padded * kb);
+    if (h->kprec == PREC_DF) {
+        ALLOC(h->Ulo[0], h->padded * 4);
+        ALLOC(h->Ulo[1], h->padded * 4);
+    }
+    if (h->vark) {
+        ALLOC(h->wx64, h->padded * 8);
+        ALLOC(h->wy64, h->padded * 8);
+        ALLOC(h->wz64, h->padded * 8);
+        ALLOC(h->invd64, h->padded * 8);
+        ALLOC(h->wx32, h->padded * 4);
+        ALLOC(h->wy32, h->padded * 4);
+        ALLOC(h->wz32, h->padded * 4);
+        ALLOC(h->invd32, h->padded * 4);
+    }
+    ALLOC(h->st, sizeof(DevState));
+    h->partials_cap = generic_partials_needed(g);
+    ALLOC(h->partials, (size_t)h->partials_cap * sizeof(double));
+    h->trace_cap = o.trace_capacity > 0 ? o.trace_capacity : 1;
+    ALLOC(h->trace_level, (size_t)h->trace_cap * sizeof(int32_t));
+    ALLOC(h->trace_rn, (size_t)h->trace_cap * sizeof(double));
+    ALLOC(h->sched, (size_t)h->trace_cap * sizeof(int32_t));
+    if (h->user_prec == SRJ_PREC_MIXED) {
+        ALLOC(h->opartials, (size_t)outer_partials_needed(g) * sizeof(double));
+        ALLOC(h->oticket, sizeof(unsigned int));
+        ALLOC(h->onorm2, sizeof(double));
+    }
+#undef ALLOC
+    if (cudaMallocHost((void **)&h->h_st, sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost((void **)&h->h_onorm2, sizeof(double)) != cudaSuccess) {
+        srj_destroy(h);
+        return SRJ_ENOMEM;
+    }
+    cudaStream_t s = h->stream;
+    srj_status rc = SRJ_OK;
+    auto ck = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && rc == SRJ_OK) {
+            rc = SRJ_ECUDA;
+            h->err = std::string(what) + ": " + cudaGetErrorString(e);
+        }
+    };
+    ck(cudaMemcpyAsync(h->w64, w.data(), kTotalOmegas * sizeof(double), cudaMemcpyHostToDevice, s),
+       "upload w64");
+    ck(cudaMemcpyAsync(h->w32, wf.data(), kTotalOmegas * sizeof(float), cudaMemcpyHostToDevice, s),
+       "upload w32");
+    // padding columns must read as zero; iterate buffers start at zero
+    for (void *p : {h->F, h->U[0], h->U[1]}) ck(cudaMemsetAsync(p, 0, h->padded * kb, s), "memset");
+    for (void *p : {h->Ulo[0], h->Ulo[1]})
+        if (p) ck(cudaMemsetAsync(p, 0, h->padded * 4, s), "memset");
+    ck(cudaMemsetAsync(h->st, 0, sizeof(DevState), s), "memset");
+    if (h->oticket) ck(cudaMemsetAsync(h->oticket, 0, sizeof(unsigned int), s), "memset");
+    if (h->vark) {
+        for (void *p : {(void *)h->wx64, (void *)h->wy64, (void *)h->wz64, (void *)h->invd64})
+            ck(cudaMemsetAsync(p, 0, h->padded * 8, s), "memset");
+        for (void *p : {(void *)h->wx32, (void *)h->wy32, (void *)h->wz32, (void *)h->invd32})
+            ck(cudaMemsetAsync(p, 0, h->padded * 4, s), "memset");
+        ck(vark_faces_launch(g, stencil->k, h->wx64, h->wy64, h->wz64, h->invd64, h->wx32,
+                             h->wy32, h->wz32, h->invd32, s),
+           "face weights");
+    }
+    ck(cudaEventCreate(&h->ev0), "event");
+    ck(cudaEventCreate(&h->ev1), "event");
+    ck(cudaStreamSynchronize(s), "create sync");
+    if (rc != SRJ_OK) {
+        srj_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return SRJ_OK;
+}
+
+srj_status srj_solve(srj_handle *h, const void *f, void *u, double tol, srj_stats *stats) {
+    if (!h) return SRJ_EINVAL;
+    if (!f || !u || !(tol > 0) || !std::isfinite(tol))
+        return fail(h, SRJ_EINVAL, "srj_solve: null array or tol not a positive finite number");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    CK(cudaEventRecord(h->ev0, h->stream));
+    srj_status s;
+    if (h->user_prec == SRJ_PREC_MIXED)
+        s = solve_mixed(h, (const double *)f, (double *)u, tol, stats);
+    else
+        s = solve_plain(h, f, u, tol, h->opts.selector, h->opts.level0, 0, stats);
+    if (s == SRJ_ECUDA || s == SRJ_EINVAL) return s;
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (stats) stats->seconds = ms * 1e-3;
+    return s;
+}
+
+srj_status srj_solve_host(srj_handle *h, const void *f_host, void *u_host, double tol,
+                          srj_stats *stats) {
+    if (!h) return SRJ_EINVAL;
+    if (!f_host || !u_host) return fail(h, SRJ_EINVAL, "srj_solve_host: null array");
+    const size_t bytes = (size_t)h->npts * h->esize;
+    if (!h->dF) {
+        if (dalloc(&h->dF, bytes) != cudaSuccess || dalloc(&h->dU, bytes) != cudaSuccess)
+            return fail(h, SRJ_ENOMEM, "srj_solve_host: staging allocation");
+    }
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    CK(cudaEventRecord(h->ev0, h->stream));
+    CK(cudaMemcpyAsync(h->dF, f_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->dU, u_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    srj_status s;
+    if (h->user_prec == SRJ_PREC_MIXED)
+        s = solve_mixed(h, (const double *)h->dF, (double *)h->dU, tol, stats);
+    else
+        s = solve_plain(h, h->dF, h->dU, tol, h->opts.selector, h->opts.level0, 0, stats);
+    if (s == SRJ_ECUDA || s == SRJ_EINVAL) return s;
+    CK(cudaMemcpyAsync(u_host, h->dU, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (stats) stats->seconds = ms * 1e-3;
+    return s;
+}
+
+srj_status srj_run_levels(srj_handle *h, const void *f, void *u, const int32_t *levels,
+                          int64_t ncycles, double *rn_out) {
+    if (!h) return SRJ_EINVAL;
+    if (!f || !u || !levels || ncycles < 1)
+        return fail(h, SRJ_EINVAL, "srj_run_levels: bad arguments");
+    if (h->user_prec == SRJ_PREC_MIXED)
+        return fail(h, SRJ_EUNSUPPORTED, "srj_run_levels: F64 or F32 precision only");
+    if (ncycles > h->trace_cap)
+        return fail(h, SRJ_EINVAL, "srj_run_levels: more cycles than trace_capacity");
+    long long total = 0;
+    for (int64_t c = 0; c < ncycles; ++c) {
+        if (levels[c] < 0 || levels[c] > kMaxLevel)
+            return fail(h, SRJ_EINVAL, "srj_run_levels: level outside [0, 24]");
+        total += kLevelM[levels[c]];
+    }
+    // next_level() reads sched[cycles] after cycle `cycles` completes
+    CK(cudaMemcpyAsync(h->sched, levels, (size_t)ncycles * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, h->stream));
+    const long long saved = h->opts.max_sweeps;
+    h->opts.max_sweeps = total + 1;
+    srj_stats stats{};
+    srj_status s = solve_plain(h, f, u, -1.0, DSEL_SCHEDULE, levels[0], (int)ncycles, &stats);
+    h->opts.max_sweeps = saved;
+    if (s == SRJ_ECUDA) return s;
+    if (rn_out) {
+        CK(cudaMemcpy(rn_out, h->trace_rn, (size_t)ncycles * sizeof(double),
+                      cudaMemcpyDeviceToHost));
+    }
+    return stats.cycles == ncycles ? SRJ_OK : fail(h, s, "srj_run_levels: schedule cut short");
+}
+
+srj_status srj_residual_norm(srj_handle *h, const void *f, const void *u, double *out) {
+    if (!h) return SRJ_EINVAL;
+    if (!f || !u || !out) return fail(h, SRJ_EINVAL, "srj_residual_norm: null argument");
+    if (h->user_prec == SRJ_PREC_MIXED)
+        return fail(h, SRJ_EUNSUPPORTED, "srj_residual_norm: F64 or F32 precision only");
+    cudaStream_t st = h->stream;
+    CK(copy_in_launch(h->kprec, h->geo, f, h->F, st));
+    CK(copy_in_launch(h->kprec, h->geo, u, h->U[0], st));
+    init_state(h, *h->h_st, 1.0, SRJ_TOL_REL, DSEL_HEURISTIC, 0, 0, 0, 0, 0);
+    CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
+    PassLaunch a = make_launch(h, false);
+    CK(generic_pass_launch(h->kprec, h->vark, a, st));
+    CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *out = h->h_st->r0;
+    return SRJ_OK;
+}
+
+int64_t srj_get_trace(const srj_handle *h, int32_t *levels, double *rn, int64_t capacity) {
+    if (!h || capacity < 0) return -1;
+    const int64_t n = h->last_cycles < capacity ? h->last_cycles : capacity;
+    const int64_t m = n < h->trace_cap ? n : h->trace_cap;
+    if (m > 0) {
+        if (levels &&
+            cudaMemcpy(levels, h->trace_level, m * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+                cudaSuccess)
+            return -1;
+        if (rn && cudaMemcpy(rn, h->trace_rn, m * sizeof(double), cudaMemcpyDeviceToHost) !=
+                      cudaSuccess)
+            return -1;
+    }
+    return h->last_cycles;
+}
+
+const char *srj_last_error(const srj_handle *h) {
+    if (!h) return "srj: invalid handle";
+    return h->err.empty() ? "" : h->err.c_str();
+}
+
+srj_status srj_destroy(srj_handle *h) {
+    if (!h) return SRJ_EINVAL;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (void *p : {(void *)h->w64, (void *)h->w32, h->F, h->U[0], h->U[1], h->Ulo[0], h->Ulo[1],
+                    (void *)h->wx64, (void *)h->wy64, (void *)h->wz64, (void *)h->invd64,
+                    (void *)h->wx32, (void *)h->wy32, (void *)h->wz32, (void *)h->invd32,
+                    (void *)h->st, (void *)h->partials, (void *)h->trace_level,
+                    (void *)h->trace_rn, (void *)h->sched, (void *)h->opartials,
+                    (void *)h->oticket, (void *)h->onorm2, h->dF, h->dU})
+        dfree(p);
+    if (h->h_st) cudaFreeHost(h->h_st);
+    if (h->h_onorm2) cudaFreeHost(h->h_onorm2);
+    delete h;
+    return SRJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// pass_common.cuh -- device-side cycle bookkeeping shared by every SRJ pass
+// kernel (included by each kernel translation unit; everything is
+// file-local).
+//
+// Each pass reads the solve state at its start (plan_pass), does its sweeps
+// and/or residual, and the last CTA to take a ticket folds the per-CTA
+// residual partials in a fixed order and advances the state (advance_state):
+// cycle bookkeeping, ratio = r_after / r_before, convergence test and the
+// next level by Sec. 3, Alg. 1.  No CTA ever waits for another.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "srj_internal.h"
+
+namespace srj {
+namespace {
+
+// ----------------------------------------------------------- state decisions
+struct PassPlan {
+    int run;     // 0: solve finished, nothing to do
+    int resid;   // 1: this pass computes the residual norm
+    int nsw;     // sweeps done by this pass (0 or 1 here)
+    int cur;     // source buffer
+    int woff;    // index of this sweep's factor in the tables
+};
+
+__device__ __forceinline__ PassPlan plan_pass(const PassLaunch &a, int depth) {
+    const DevState *st = a.st;
+    PassPlan p{};
+    if (st->status != DST_RUNNING) return p;
+    p.run = 1;
+    p.cur = st->cur;
+    if (st->phase == 0) {
+        p.resid = 1;
+        return p;
+    }
+    const int M = a.lvl_m[st->level];
+    const int rem = M - st->k;
+    // A cycle of M sweeps takes floor(M / depth) + 1 passes; the last one does
+    // rem < depth sweeps and then the residual of the cycle's final state.
+    p.nsw = rem >= depth ? depth : rem;
+    p.resid = rem < depth ? 1 : 0;
+    p.woff = a.lvl_off[st->level] + st->k;
+    return p;
+}
+
+__device__ __forceinline__ int next_level(const DevState *st, const SolveCfg &cfg,
+                                          double ratio, int level) {
+    const int top = st->max_level;
+    switch (st->selector) {
+        case DSEL_INCREASING:
+            return level < top ? level + 1 : level;
+        case DSEL_FIXED:
+            return st->fixed_level;
+        case DSEL_SCHEDULE:
+            return (st->cycles < st->nsched) ? cfg.sched[st->cycles] : level;
+        default:  // Alg. 1 (also the fallback of the learned selector)
+            if (ratio > 0.4) return level < top ? level + 1 : level;
+            if (ratio < 0.4 && ratio > 0.2) return level > 0 ? level - 1 : level;
+            return level;
+    }
+}
+
+// Executed by one thread of the last CTA of a pass.
+__device__ void advance_state(DevState *st, const SolveCfg &cfg, const PassPlan &p,
+                              double norm2) {
+    st->passes += 1;
+    if (p.nsw > 0) {
+        st->cur ^= 1;
+        st->k += p.nsw;
+        st->sweeps += p.nsw;
+    }
+    if (!p.resid) return;
+    const double rn = sqrt(norm2);
+    if (st->phase == 0) {
+        st->phase = 1;
+        st->r0 = rn;
+        st->rprev = rn;
+        st->rn = rn;
+        if (!isfinite(rn)) st->status = DST_DIVERGED;
+        else if (rn == 0.0 || (st->tol_kind == SRJ_TOL_ABS && rn < st->tol))
+            st->status = DST_CONVERGED;
+        return;
+    }
+    const double ratio = rn / st->rprev;
+    st->rprev = rn;
+    st->rn = rn;
+    const long long c = st->cycles;
+    const long long ti = c + st->trace_base;
+    if (ti < cfg.trace_cap) {
+        cfg.trace_level[ti] = st->level;
+        cfg.trace_rn[ti] = rn;
+    }
+    st->cycles = c + 1;
+    const double test = (st->tol_kind == SRJ_TOL_ABS) ? rn : rn / st->r0;
+    if (!isfinite(rn)) {
+        st->status = DST_DIVERGED;
+    } else if (test < st->tol) {
+        st->status = DST_CONVERGED;
+    } else if (st->selector == DSEL_SCHEDULE && st->cycles >= st->nsched) {
+        st->status = DST_DONE;
+    } else if (st->stall_stop && ratio >= 1.0) {
+        st->status = DST_STALLED;
+    } else if (st->sweeps >= st->max_sweeps) {
+        st->status = DST_NOTCONV;
+    } else {
+        st->level = next_level(st, cfg, ratio, st->level);
+        st->k = 0;
+    }
+}
+
+// Deterministic block sum: butterfly within warps, then warps in order.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double s_warp[32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nthreads = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) s_warp[tid >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < (nthreads + 31) / 32; ++w) t += s_warp[w];
+    return t;  // valid in thread 0
+}
+
+// Ticket + last-CTA finish, shared by all pass kernels.  block_total is the
+// CTA's partial (valid in thread 0).  Returns after the bookkeeping.
+__device__ void finish_pass(const PassLaunch &a, const PassPlan &p, double block_total) {
+    __shared__ int s_last;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (tid == 0) {
+        if (p.resid) a.partials[bid] = block_total;
+        __threadfence();
+        const unsigned int t = atomicAdd(&a.st->ticket, 1u);
+        s_last = (t == nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double norm2 = 0.0;
+    if (p.resid && tid < 32) {
+        // fixed assignment of partials to lanes, fixed butterfly: deterministic
+        double acc = 0.0;
+        const volatile double *part = a.partials;
+        for (unsigned int i = tid; i < nblocks; i += 32) acc += part[i];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        norm2 = acc;
+    }
+    if (tid == 0) {
+        DevState *st = a.st;
+        advance_state(st, a.cfg, p, norm2);
+        st->ticket = 0;
+        __threadfence();
+        if (a.cfg.use_cond && st->status != DST_RUNNING)
+            cudaGraphSetConditional(a.cfg.cond, 0);
+    }
+}
+
+}  // namespace
+}  // namespace srj

@@ -1,0 +1,171 @@
+// srj_internal.h -- declarations shared by the translation units of libsrj.so.
+//
+// Internal data layout (all working arrays are library-owned):
+//   padded layout: index = x + pitch * y + plane * z, pitch = round_up(nx, 32)
+//   elements, plane = pitch * ny.  Columns x in [nx, pitch) are zero and stay
+//   zero (they act as the x = nx Dirichlet ghost column).  Points outside the
+//   interior are zero (Dirichlet).  1D grids use ny = nz = 1, 2D nz = 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/srj.h"
+
+namespace srj {
+
+constexpr int kMaxLevel = 24;
+constexpr int kNumLevels = 25;
+constexpr int kTotalOmegas = 9710;  // sum of M over the 25 levels
+
+// App. B table (scheme level -> M) and the offset of each level's factors in
+// the concatenated factor table.  Defined in schemes.cpp.
+extern const int kLevelM[kNumLevels];
+int level_offset(int level);
+// Sec. 2 Eq. (srj-relaxation-parameters) + Leja order; fills out[kTotalOmegas].
+void build_omega_table(double *out);
+int scheme_omegas(int level, double *out, int capacity);
+
+// Selector values used on the device (srj_selector plus internal ones).
+enum DevSelector : int32_t {
+    DSEL_HEURISTIC = 0,
+    DSEL_INCREASING = 1,
+    DSEL_FIXED = 2,
+    DSEL_MLP = 3,
+    DSEL_SCHEDULE = 4  // explicit level list (srj_run_levels)
+};
+
+// Status values of a device-side solve.
+enum DevStatus : int32_t {
+    DST_RUNNING = 0,
+    DST_CONVERGED = 1,
+    DST_NOTCONV = 2,
+    DST_DIVERGED = 3,
+    DST_STALLED = 4,  // inner solve of mixed precision: a cycle raised the residual
+    DST_DONE = 5      // explicit schedule finished
+};
+
+// Per-solve state in device memory.  The host writes the whole struct (the
+// settings and the initial values) before each solve; afterwards it is written
+// only by the last CTA of each pass (finish in kernels_generic.cu) and read by
+// every CTA at the start of a pass.  Keeping the settings here (not in kernel
+// arguments) lets one instantiated CUDA graph serve every solve on a handle.
+struct DevState {
+    // settings of this solve
+    double tol;
+    long long max_sweeps;
+    int32_t tol_kind;     // srj_tol_kind
+    int32_t selector;     // DevSelector
+    int32_t fixed_level;
+    int32_t max_level;
+    int32_t stall_stop;   // 1: stop when a cycle's ratio >= 1 (inner of MIXED)
+    int32_t nsched;       // DSEL_SCHEDULE: number of scheduled cycles
+    // running state
+    int32_t level;        // level of the cycle in progress
+    int32_t k;            // sweeps of the current cycle already done
+    int32_t cur;          // ping-pong buffer holding the current iterate
+    int32_t status;       // DevStatus
+    int32_t phase;        // 0: initial residual r0 not yet taken
+    int32_t trace_base;   // first trace slot of this solve
+    long long sweeps, cycles, passes;
+    double r0, rprev, rn;
+    unsigned int ticket;  // CTAs finished in the current pass
+    unsigned int pad1;
+};
+
+// Static per-handle pointers passed by value to the pass kernels.
+struct SolveCfg {
+    const int32_t *sched;  // DSEL_SCHEDULE level list
+    int32_t *trace_level;
+    double *trace_rn;
+    int32_t trace_cap;
+    int32_t use_cond;      // 1 when launched inside a conditional while node
+    cudaGraphConditionalHandle cond;
+    const float *mlp_w;    // learned selector weights (nullptr unless loaded)
+};
+
+// Grid geometry and constant coefficients.
+struct GridGeo {
+    int32_t dim;
+    int32_t nx, ny, nz;
+    long long pitch, plane;
+    double cx, cy, cz;  // eps_a / h_a^2
+    double diag;        // 2 (cx + cy + cz) for constant coefficients
+};
+
+enum Prec : int32_t { PREC_F64 = 0, PREC_F32 = 1, PREC_DF = 2 };
+
+// Buffers of one iterate pair plus right-hand side, typeless.
+//   F64: f = double*, u = double*;  F32: float*;  DF: f float*, u = hi float*,
+//   ulo = lo float*.
+struct IterBufs {
+    const void *f;
+    void *u[2];
+    void *ulo[2];
+    // variable coefficients (nullptr for constant): face weights eps*kf/h^2 on
+    // the +x, +y, +z face of each cell and 1/D, in the padded layout, element
+    // type double for F64, float for F32 / DF.
+    const void *wx, *wy, *wz, *invd;
+};
+
+struct PassLaunch {
+    GridGeo geo;
+    IterBufs bufs;
+    DevState *st;
+    double *partials;      // one FP64 slot per CTA
+    int partials_cap;
+    const double *w64;     // device factor tables (kTotalOmegas)
+    const float *w32;
+    SolveCfg cfg;
+    int lvl_m[kNumLevels];    // App. B: M of each level
+    int lvl_off[kNumLevels];  // offset of each level's factors in w64 / w32
+};
+
+// Launch helpers implemented in kernels_generic.cu.  Each returns the CUDA
+// error of the launch (cudaSuccess when queued).
+struct GenericPlan {
+    dim3 grid, block;
+    int zchunk;
+    void *kernel;  // __global__ entry for graph nodes
+};
+GenericPlan generic_plan(int prec, const GridGeo &g, bool vark);
+int generic_partials_needed(const GridGeo &g);
+cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a,
+                                cudaStream_t s);
+cudaError_t add_generic_pass_node(int prec, bool vark, const PassLaunch &a,
+                                  cudaGraph_t body);
+
+// Whole-grid helpers (kernels_generic.cu).
+// FP64 outer residual of the mixed-precision path on dense user arrays:
+// writes r into the padded FP32 inner right-hand side, ||r||^2 partials and a
+// last-CTA total into *out_norm2 (with its own ticket counter).
+struct OuterArgs {
+    GridGeo geo;
+    const double *f, *u;  // dense user arrays
+    double *u_out;        // dense user array (update)
+    float *r32;           // padded inner rhs
+    const float *ehi[2], *elo[2];  // padded inner iterate pair
+    const DevState *inner;         // inner solve state (selects ehi[cur])
+    const double *wx, *wy, *wz, *invd;  // FP64 face weights (padded) or null
+    double *partials;
+    unsigned int *ticket;
+    double *out_norm2;
+};
+cudaError_t outer_residual_launch(const OuterArgs &a, cudaStream_t s);
+cudaError_t outer_update_launch(const OuterArgs &a, cudaStream_t s);
+int outer_partials_needed(const GridGeo &g);
+
+// Dense <-> padded copies (kernels_generic.cu).  copy_out picks the padded
+// buffer holding the iterate from st->cur on the device.
+cudaError_t copy_in_launch(int prec, const GridGeo &g, const void *dense, void *padded,
+                           cudaStream_t s);
+cudaError_t copy_out_launch(int prec, const GridGeo &g, const DevState *st, void *const *pads,
+                            void *dense, cudaStream_t s);
+
+// Face weights of the variable-coefficient operator (kernels_generic.cu).
+cudaError_t vark_faces_launch(const GridGeo &g, const double *k, double *wx,
+                              double *wy, double *wz, double *invd,
+                              float *wx32, float *wy32, float *wz32,
+                              float *invd32, cudaStream_t s);
+
+}  // namespace srj

@@ -1,0 +1,212 @@
+"""ctypes binding of libsrj.so (include/srj.h), same names as the C ABI.
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Device arrays are passed as raw pointers (``tensor.data_ptr()``);
+PyTorch is used by callers for device memory and streams only.  Importing
+this module loads the library and raises if it is missing -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import _build
+
+SRJ_OK, SRJ_EINVAL, SRJ_ENOMEM, SRJ_ECUDA, SRJ_ENOTCONV, SRJ_EDIVERGED, SRJ_ETIMEOUT, \
+    SRJ_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["SRJ_OK", "SRJ_EINVAL", "SRJ_ENOMEM", "SRJ_ECUDA", "SRJ_ENOTCONV",
+                "SRJ_EDIVERGED", "SRJ_ETIMEOUT", "SRJ_EUNSUPPORTED"]
+SRJ_SEL_HEURISTIC, SRJ_SEL_INCREASING, SRJ_SEL_FIXED, SRJ_SEL_MLP = range(4)
+SRJ_PREC_F64, SRJ_PREC_F32, SRJ_PREC_MIXED = range(3)
+SRJ_TOL_REL, SRJ_TOL_ABS = range(2)
+
+# every entry point include/srj.h declares
+EXPORTS = ["srj_version", "srj_level_m", "srj_scheme_omegas", "srj_create", "srj_solve",
+           "srj_solve_host", "srj_run_levels", "srj_residual_norm", "srj_get_trace",
+           "srj_last_error", "srj_destroy"]
+
+
+class srj_grid(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int64 * 3), ("h", C.c_double * 3)]
+
+
+class srj_stencil(C.Structure):
+    _fields_ = [("eps", C.c_double * 3), ("k", C.c_void_p)]
+
+
+class srj_opts(C.Structure):
+    _fields_ = [("selector", C.c_int32), ("precision", C.c_int32), ("tol_kind", C.c_int32),
+                ("level0", C.c_int32), ("fixed_level", C.c_int32), ("max_level", C.c_int32),
+                ("temporal_depth", C.c_int32), ("trace_capacity", C.c_int32),
+                ("max_sweeps", C.c_int64), ("inner_tol", C.c_double)]
+
+
+class srj_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("final_level", C.c_int32), ("sweeps", C.c_int64),
+                ("cycles", C.c_int64), ("outer", C.c_int64), ("passes", C.c_int64),
+                ("r0", C.c_double), ("rn", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsrj.so (building it in-tree with nvcc if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError("libsrj.so is not built: run __graft_entry__.build()")
+        _build.build()
+    L = C.CDLL(path)
+    H = C.c_void_p
+    L.srj_version.restype = C.c_char_p
+    L.srj_level_m.argtypes = [C.c_int32]
+    L.srj_level_m.restype = C.c_int32
+    L.srj_scheme_omegas.argtypes = [C.c_int32, C.POINTER(C.c_double), C.c_int32]
+    L.srj_scheme_omegas.restype = C.c_int32
+    L.srj_create.argtypes = [C.POINTER(srj_grid), C.POINTER(srj_stencil), C.POINTER(srj_opts),
+                             C.c_void_p, C.POINTER(H)]
+    L.srj_create.restype = C.c_int
+    L.srj_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(srj_stats)]
+    L.srj_solve.restype = C.c_int
+    L.srj_solve_host.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(srj_stats)]
+    L.srj_solve_host.restype = C.c_int
+    L.srj_run_levels.argtypes = [H, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_int64,
+                                 C.POINTER(C.c_double)]
+    L.srj_run_levels.restype = C.c_int
+    L.srj_residual_norm.argtypes = [H, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
+    L.srj_residual_norm.restype = C.c_int
+    L.srj_get_trace.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_int64]
+    L.srj_get_trace.restype = C.c_int64
+    L.srj_last_error.argtypes = [H]
+    L.srj_last_error.restype = C.c_char_p
+    L.srj_destroy.argtypes = [H]
+    L.srj_destroy.restype = C.c_int
+    _lib = L
+    return L
+
+
+class SrjError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s%s" % (name, (": " + msg) if msg else ""))
+
+
+def srj_version() -> str:
+    return load().srj_version().decode()
+
+
+def srj_level_m(level: int) -> int:
+    return load().srj_level_m(level)
+
+
+def srj_scheme_omegas(level: int):
+    import numpy as np
+    out = np.zeros(2362)
+    m = load().srj_scheme_omegas(level, out.ctypes.data_as(C.POINTER(C.c_double)), 2362)
+    if m < 0:
+        raise SrjError(SRJ_EINVAL, "bad level")
+    return out[:m].copy()
+
+
+def _grid(n, h=None):
+    g = srj_grid()
+    g.dim = len(n)
+    for a in range(3):
+        g.n[a] = int(n[a]) if a < len(n) else 1
+        g.h[a] = float(h[a]) if (h is not None and a < len(n)) else 0.0
+    return g
+
+
+def srj_create(n, h=None, eps=None, k_ptr=None, selector=SRJ_SEL_HEURISTIC,
+               precision=SRJ_PREC_F64, tol_kind=SRJ_TOL_REL, level0=0, fixed_level=0,
+               max_level=0, temporal_depth=0, trace_capacity=0, max_sweeps=0, inner_tol=0.0,
+               stream=None):
+    """Returns an opaque handle (int).  ``k_ptr`` is a device pointer (int) or None."""
+    L = load()
+    g = _grid(n, h)
+    st = srj_stencil()
+    for a in range(3):
+        st.eps[a] = float(eps[a]) if (eps is not None and a < len(eps)) else 0.0
+    st.k = k_ptr
+    o = srj_opts(selector, precision, tol_kind, level0, fixed_level, max_level, temporal_depth,
+                 trace_capacity, max_sweeps, inner_tol)
+    hnd = C.c_void_p()
+    rc = L.srj_create(C.byref(g), C.byref(st), C.byref(o), stream, C.byref(hnd))
+    if rc != SRJ_OK:
+        raise SrjError(rc, "srj_create")
+    return hnd.value
+
+
+def _check(h, rc, what):
+    if rc not in (SRJ_OK,):
+        raise SrjError(rc, "%s: %s" % (what, load().srj_last_error(h).decode()))
+
+
+def srj_solve(h, f_ptr, u_ptr, tol, raise_on_notconv=False):
+    s = srj_stats()
+    rc = load().srj_solve(h, f_ptr, u_ptr, float(tol), C.byref(s))
+    if rc in (SRJ_ENOTCONV, SRJ_EDIVERGED) and not raise_on_notconv:
+        return s.as_dict()
+    _check(h, rc, "srj_solve")
+    return s.as_dict()
+
+
+def srj_solve_host(h, f_host_ptr, u_host_ptr, tol, raise_on_notconv=False):
+    s = srj_stats()
+    rc = load().srj_solve_host(h, f_host_ptr, u_host_ptr, float(tol), C.byref(s))
+    if rc in (SRJ_ENOTCONV, SRJ_EDIVERGED) and not raise_on_notconv:
+        return s.as_dict()
+    _check(h, rc, "srj_solve_host")
+    return s.as_dict()
+
+
+def srj_run_levels(h, f_ptr, u_ptr, levels):
+    import numpy as np
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    rn = np.zeros(len(lv))
+    rc = load().srj_run_levels(h, f_ptr, u_ptr, lv.ctypes.data_as(C.POINTER(C.c_int32)), len(lv),
+                               rn.ctypes.data_as(C.POINTER(C.c_double)))
+    _check(h, rc, "srj_run_levels")
+    return rn
+
+
+def srj_residual_norm(h, f_ptr, u_ptr) -> float:
+    out = C.c_double()
+    rc = load().srj_residual_norm(h, f_ptr, u_ptr, C.byref(out))
+    _check(h, rc, "srj_residual_norm")
+    return out.value
+
+
+def srj_get_trace(h, capacity=100000):
+    import numpy as np
+    lv = np.zeros(capacity, dtype=np.int32)
+    rn = np.zeros(capacity)
+    n = load().srj_get_trace(h, lv.ctypes.data_as(C.POINTER(C.c_int32)),
+                             rn.ctypes.data_as(C.POINTER(C.c_double)), capacity)
+    if n < 0:
+        raise SrjError(SRJ_EINVAL, "srj_get_trace")
+    m = min(n, capacity)
+    return lv[:m].copy(), rn[:m].copy()
+
+
+def srj_last_error(h) -> str:
+    return load().srj_last_error(h).decode()
+
+
+def srj_destroy(h):
+    rc = load().srj_destroy(h)
+    if rc != SRJ_OK:
+        raise SrjError(rc, "srj_destroy")

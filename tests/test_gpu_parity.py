@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle
+on the same seeded inputs.
+
+Tolerances:
+ * FP64 -- relative 1e-10 on the solution and per-cycle residual norms, and
+   identical level sequences (a decision may differ only where the oracle's
+   ratio lies within 1e-9 of a threshold 0.2 / 0.4; the tests check there is
+   no such near-tie instead of skipping).
+ * FP32 -- a forward-error bound from the arithmetic: each sweep rounds about
+   eight FP32 operations (relative eps32 each) and a rounding error committed
+   inside a cycle of M factors is amplified by at most the partial-product
+   growth of the cycle, which the application order keeps below M^2 (pinned in
+   test_oracle_schemes); hence |u32 - u64| <= 8 eps32 sum_cycles M^3 max|u|.
+ * MIXED -- both solutions satisfy ||f - A u|| < tol ||f - A u0||, so each is
+   within ||r|| / lambda_min(A) of the exact solution (A is SPD); lambda_min
+   in closed form for constant coefficients and bounded below by
+   min(k) lambda_min(constant) for variable k.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2011_06636_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_06636_gb300 import _build, srj
+    _build.build()
+    srj.load(build_if_missing=False)
+    torch.cuda.init()
+    return srj
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def make(S, n, prec, **kw):
+    k = kw.pop("k", None)
+    kt = None
+    if k is not None:
+        kt = dev(k)
+        kw["k_ptr"] = kt.data_ptr()
+    h = S.srj_create(n, precision=prec, **kw)
+    return h, kt
+
+
+def lam_min_const(n, eps=None):
+    eps = eps or [1.0] * len(n)
+    return sum(eps[a] * 4 * (n[a] + 1) ** 2 * math.sin(math.pi / (2 * (n[a] + 1))) ** 2
+               for a in range(len(n)))
+
+
+def near_tie(rns, r0):
+    prev = r0
+    for r in rns:
+        ratio = r / prev
+        prev = r
+        if abs(ratio - 0.4) < 1e-9 or abs(ratio - 0.2) < 1e-9:
+            return True
+    return False
+
+
+CASES = [
+    ("1d_1024_sines", [1024], None, None),
+    ("1d_1", [1], None, None),
+    ("1d_37", [37], None, None),
+    ("2d_64x48_aniso", [64, 48], [0.05, 1.0], None),
+    ("2d_33x70", [33, 70], None, None),
+    ("3d_20x18x16", [20, 18, 16], None, None),
+    ("3d_17x9x12_vark", [17, 9, 12], [1.0, 0.5, 2.0], "vark"),
+    ("2d_40x31_vark", [40, 31], None, "vark"),
+]
+
+
+def case_inputs(name, n, kind):
+    if name.startswith("1d_1024"):
+        f = inputs.poisson1d_sines(1024, seed=0)
+    else:
+        f = inputs.uniform_rhs(n, seed=len(name)).ravel()
+    k = inputs.lognormal_k(n, seed=3, corr=4.0) if kind == "vark" else None
+    return f.ravel(), k
+
+
+@pytest.mark.parametrize("name,n,eps,kind", CASES, ids=[c[0] for c in CASES])
+def test_residual_norm_f64(S, orc, name, n, eps, kind):
+    f, k = case_inputs(name, n, kind)
+    u = np.random.default_rng(5).standard_normal(f.size)
+    h, kt = make(S, n, S.SRJ_PREC_F64, eps=eps, k=k)
+    try:
+        got = S.srj_residual_norm(h, dev(f).data_ptr(), dev(u).data_ptr())
+    finally:
+        S.srj_destroy(h)
+    ref = orc.residual_norm(orc.Problem(n, eps=eps, k=k), u, f)
+    assert abs(got - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("name,n,eps,kind", CASES, ids=[c[0] for c in CASES])
+def test_fixed_schedule_f64(S, orc, name, n, eps, kind):
+    """Sweeps and per-cycle residuals for an explicit level list."""
+    f, k = case_inputs(name, n, kind)
+    levels = [0, 1, 2, 3, 5, 8, 11, 9, 13]
+    u0 = np.zeros(f.size)
+    h, kt = make(S, n, S.SRJ_PREC_F64, eps=eps, k=k)
+    try:
+        ud = dev(u0)
+        rn = S.srj_run_levels(h, dev(f).data_ptr(), ud.data_ptr(), levels)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    uo, rno = orc.run_levels(orc.Problem(n, eps=eps, k=k), f, u0, levels)
+    assert np.max(np.abs(ug - uo)) <= 1e-10 * np.max(np.abs(uo))
+    assert np.max(np.abs(rn - rno) / rno) <= 1e-10
+
+
+@pytest.mark.parametrize("name,n,eps,kind", CASES, ids=[c[0] for c in CASES])
+def test_heuristic_solve_f64(S, orc, name, n, eps, kind):
+    """Whole solve with Alg. 1: identical level sequence and sweep count,
+    solution within 1e-10."""
+    f, k = case_inputs(name, n, kind)
+    P = orc.Problem(n, eps=eps, k=k)
+    ref = orc.srj_solve(P, f, tol=1e-8)
+    assert not near_tie(ref["rns"], ref["r0"])
+    h, kt = make(S, n, S.SRJ_PREC_F64, eps=eps, k=k)
+    try:
+        ud = dev(np.zeros(f.size))
+        st = S.srj_solve(h, dev(f).data_ptr(), ud.data_ptr(), 1e-8)
+        lv, rn = S.srj_get_trace(h)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    assert st["status"] == S.SRJ_OK
+    assert st["sweeps"] == ref["sweeps"] and st["cycles"] == ref["cycles"]
+    assert list(lv) == list(ref["levels"])
+    assert np.max(np.abs(rn - ref["rns"]) / ref["rns"]) <= 1e-10
+    assert np.max(np.abs(ug - ref["u"])) <= 1e-10 * np.max(np.abs(ref["u"]))
+
+
+def test_paper_n100_pattern_on_gpu(S, orc):
+    """Sec. 4.1: N=100, b=1, abs tol 1e-7 -- same iterations and level pattern
+    as the oracle (which is pinned to the paper's ~1000 / levels 10-11)."""
+    N = 100
+    f = np.ones(N)
+    ref = orc.srj_solve(orc.Problem([N]), f, tol=1e-7, tol_kind="abs")
+    for rule, sel in (("heuristic", S.SRJ_SEL_HEURISTIC), ("increasing", S.SRJ_SEL_INCREASING)):
+        ref = orc.srj_solve(orc.Problem([N]), f, tol=1e-7, tol_kind="abs", rule=rule)
+        h, _ = make(S, [N], S.SRJ_PREC_F64, selector=sel, tol_kind=S.SRJ_TOL_ABS)
+        try:
+            st = S.srj_solve(h, dev(f).data_ptr(), dev(np.zeros(N)).data_ptr(), 1e-7)
+            lv, _ = S.srj_get_trace(h)
+        finally:
+            S.srj_destroy(h)
+        assert st["status"] == S.SRJ_OK
+        assert st["sweeps"] == ref["sweeps"]
+        assert list(lv) == list(ref["levels"])
+
+
+@pytest.mark.parametrize("name,n,eps,kind", CASES[:6], ids=[c[0] for c in CASES[:6]])
+def test_fixed_schedule_f32_within_bound(S, orc, name, n, eps, kind):
+    f, k = case_inputs(name, n, kind)
+    levels = [0, 1, 2, 3, 4, 6, 8]
+    h, _ = make(S, n, S.SRJ_PREC_F32, eps=eps)
+    try:
+        ud = dev(np.zeros(f.size), torch.float32)
+        S.srj_run_levels(h, dev(f, torch.float32).data_ptr(), ud.data_ptr(), levels)
+        ug = ud.cpu().numpy().astype(np.float64)
+    finally:
+        S.srj_destroy(h)
+    f32 = f.astype(np.float32).astype(np.float64)
+    uo, _ = orc.run_levels(orc.Problem(n, eps=eps), f32, np.zeros(f.size), levels)
+    bound = 8 * EPS32 * sum(S.srj_level_m(l) ** 3 for l in levels) * np.max(np.abs(uo))
+    assert np.max(np.abs(ug - uo)) <= bound
+
+
+@pytest.mark.parametrize("name,n,eps,kind", CASES, ids=[c[0] for c in CASES])
+def test_mixed_precision_solve(S, orc, name, n, eps, kind):
+    """FP32-arithmetic inner SRJ inside FP64 refinement reaches 1e-8 and lies
+    within the residual bound of the FP64 oracle's solution."""
+    f, k = case_inputs(name, n, kind)
+    P = orc.Problem(n, eps=eps, k=k)
+    ref = orc.srj_solve(P, f, tol=1e-8)
+    h, kt = make(S, n, S.SRJ_PREC_MIXED, eps=eps, k=k)
+    try:
+        ud = dev(np.zeros(f.size))
+        st = S.srj_solve(h, dev(f).data_ptr(), ud.data_ptr(), 1e-8)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    assert st["status"] == S.SRJ_OK, st
+    rn_true = orc.residual_norm(P, ug, f)
+    assert rn_true / ref["r0"] < 1e-8
+    assert abs(st["rn"] - rn_true) <= 1e-6 * rn_true + 1e-12 * ref["r0"]
+    lam = lam_min_const(n, eps) * (float(np.min(k)) if k is not None else 1.0)
+    assert np.linalg.norm(ug - ref["u"]) <= (rn_true + ref["rn"]) / lam * (1 + 1e-6)
+
+
+def test_solve_host_matches_device(S):
+    n = [96, 80]
+    f = inputs.uniform_rhs(n, seed=9).ravel()
+    h, _ = make(S, n, S.SRJ_PREC_F64)
+    try:
+        ud = dev(np.zeros(f.size))
+        a = S.srj_solve(h, dev(f).data_ptr(), ud.data_ptr(), 1e-8)
+        fh = torch.as_tensor(f).pin_memory()
+        uh = torch.zeros(f.size, dtype=torch.float64).pin_memory()
+        b = S.srj_solve_host(h, fh.data_ptr(), uh.data_ptr(), 1e-8)
+    finally:
+        S.srj_destroy(h)
+    assert a["sweeps"] == b["sweeps"]
+    assert torch.equal(ud.cpu(), uh)
+
+
+def test_invalid_arguments_return_codes(S):
+    h, _ = make(S, [16, 16], S.SRJ_PREC_F64)
+    try:
+        L = S.load()
+        assert L.srj_solve(h, None, None, 1e-8, None) == S.SRJ_EINVAL
+        f = dev(np.ones(256))
+        assert L.srj_solve(h, f.data_ptr(), f.data_ptr(), -1.0, None) == S.SRJ_EINVAL
+        assert "tol" in S.srj_last_error(h)
+    finally:
+        S.srj_destroy(h)
+    with pytest.raises(S.SrjError):
+        S.srj_create([0, 4])
+    with pytest.raises(S.SrjError):
+        S.srj_create([8], level0=30)
+
+
+def test_notconv_status_and_cap(S):
+    n = [256]
+    f = np.ones(256)
+    h, _ = make(S, n, S.SRJ_PREC_F64, max_sweeps=50)
+    try:
+        st = S.srj_solve(h, dev(f).data_ptr(), dev(np.zeros(256)).data_ptr(), 1e-12)
+    finally:
+        S.srj_destroy(h)
+    assert st["status"] == S.SRJ_ENOTCONV
+    assert 50 <= st["sweeps"] < 50 + 2362
