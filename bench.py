@@ -31,6 +31,11 @@ METRIC = ("GLUP/s (% HBM roofline) and time to 1e-8 rel. residual, learned/mixed
 UNIT = "GLUP/s"
 SIDE = 4096
 TOL = 1e-8
+# FP32 instructions per grid-point update of the FP32-pair relaxation (2D,
+# constant coefficients): 4 compensated adds (11 each), 2 compensated scalings
+# (6 each), the exact product D^-1 f (2), the compensated subtraction of u (11)
+# and the update u + omega t (6 + 11).
+DF_OPS_PER_LUP = 86
 WORKLOAD = ("2D Poisson 5-point, 4096x4096 interior, zero Dirichlet, f~U[-1,1] (seed 0+rank), "
             "u0=0, rel residual 1e-8, SRJ scheme family + Alg. 1 heuristic")
 
@@ -41,6 +46,12 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def fp32_issue_peak(sm_mhz):
+    """FP32 instruction rate of the GPU: 152 SMs x 128 FP32 lanes x clock
+    (one instruction per lane per cycle, FMA counted once), in T instr/s."""
+    return 152 * 128 * sm_mhz * 1e6 / 1e12
 
 
 class Clocks:
@@ -200,13 +211,15 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(local)
     _build.build()
     srj.load(build_if_missing=False)
-    n = [SIDE, SIDE]
-    npts = SIDE * SIDE
+    side = args.side
+    n = [side, side]
+    npts = side * side
     f_np = inputs.uniform_rhs(n, seed=rank).ravel()
     stream = torch.cuda.current_stream()
     f = torch.as_tensor(f_np, device="cuda")
     u = torch.zeros(npts, dtype=torch.float64, device="cuda")
-    h = srj.srj_create(n, precision=srj.SRJ_PREC_MIXED, stream=stream.cuda_stream)
+    h = srj.srj_create(n, precision=srj.SRJ_PREC_MIXED, stream=stream.cuda_stream,
+                       temporal_depth=args.depth)
 
     def step():
         u.zero_()
@@ -236,33 +249,42 @@ def run_ours(args, rank, world):
     value = lups / (ms_max * 1e-3) / 1e9
     ok = all(s["status"] == srj.SRJ_OK for s in stats)
     # relative residual of the last solve, checked independently in FP64 torch
-    uu = u.view(SIDE, SIDE)
-    ff = f.view(SIDE, SIDE)
+    uu = u.view(side, side)
+    ff = f.view(side, side)
     up = torch.nn.functional.pad(uu, (1, 1, 1, 1))
-    hinv2 = float((SIDE + 1) ** 2)
+    hinv2 = float((side + 1) ** 2)
     Au = hinv2 * (4 * uu - up[1:-1, :-2] - up[1:-1, 2:] - up[:-2, 1:-1] - up[2:, 1:-1])
     rel_check = float(torch.linalg.norm(ff - Au) / torch.linalg.norm(ff))
 
-    # dominant kernel: inner pass; per-pass device time over the timed region
+    # dominant kernel: the inner pass.  Its per-launch time is taken as the
+    # timed device time divided by the passes (an upper bound: it includes the
+    # few outer FP64 kernels and the loop-node overhead between passes).
+    clocks = clk.summary()
     pass_ms = ms / max(passes, 1)
+    sweeps_per_pass = sweeps / max(passes, 1)
     bytes_per_pass = 20.0 * npts  # FP32-pair iterate read+write (8+8) + FP32 rhs (4)
     hbm_peak, peak_kind = peaks()
-    achieved = bytes_per_pass / (pass_ms * 1e-3) / 1e9
+    hbm_achieved = bytes_per_pass / (pass_ms * 1e-3) / 1e9
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    alu_peak = fp32_issue_peak(sm_mhz)
+    alu_achieved = DF_OPS_PER_LUP * npts * sweeps_per_pass / (pass_ms * 1e-3) / 1e12
 
     # end to end through srj_solve_host with pinned host buffers
-    fh = torch.as_tensor(f_np).pin_memory()
-    uh = torch.zeros(npts, dtype=torch.float64).pin_memory()
-    e2e_st = srj.srj_solve_host(h, fh.data_ptr(), uh.data_ptr(), TOL)
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    e2e_sweeps = 0
-    for _ in range(args.steps):
-        uh.zero_()
+    e2e_val = None
+    if not args.no_e2e:
+        fh = torch.as_tensor(f_np).pin_memory()
+        uh = torch.zeros(npts, dtype=torch.float64).pin_memory()
         e2e_st = srj.srj_solve_host(h, fh.data_ptr(), uh.data_ptr(), TOL)
-        e2e_sweeps += e2e_st["sweeps"]
-    e2e_s = allmax(world, time.perf_counter() - t0)
-    e2e_val = allsum(world, float(e2e_sweeps) * npts) / e2e_s / 1e9
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        e2e_sweeps = 0
+        for _ in range(args.steps):
+            uh.zero_()
+            e2e_st = srj.srj_solve_host(h, fh.data_ptr(), uh.data_ptr(), TOL)
+            e2e_sweeps += e2e_st["sweeps"]
+        e2e_s = allmax(world, time.perf_counter() - t0)
+        e2e_val = allsum(world, float(e2e_sweeps) * npts) / e2e_s / 1e9
     srj.srj_destroy(h)
 
     # plain FP64 SRJ with the heuristic on the same problem (comparator)
@@ -276,34 +298,75 @@ def run_ours(args, rank, world):
                 "glups": s64["sweeps"] * npts / s64["seconds"] / 1e9,
                 "status": srj.STATUS_NAMES[s64["status"]]}
 
+    # FP32 variant of the same grid: plain FP32 sweeps (temporal depth 8) over a
+    # fixed schedule that stays in FP32's stable range (levels 0..16, then 16
+    # repeated); FP32 alone floors near kappa*eps32, so it is timed per sweep,
+    # not to tolerance.
+    f32 = None
+    if not args.no_f32:
+        levels = list(range(17)) + [16] * 20
+        f32t = f.float()
+        u32 = torch.zeros(npts, dtype=torch.float32, device="cuda")
+        h32 = srj.srj_create(n, precision=srj.SRJ_PREC_F32, stream=stream.cuda_stream,
+                             trace_capacity=64)
+        srj.srj_run_levels(h32, f32t.data_ptr(), u32.data_ptr(), levels)  # warm-up
+        u32.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rn32 = srj.srj_run_levels(h32, f32t.data_ptr(), u32.data_ptr(), levels)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        srj.srj_destroy(h32)
+        sw32 = sum(srj.srj_level_m(l) for l in levels)
+        t32 = e0.elapsed_time(e1) * 1e-3
+        passes32 = sum(srj.srj_level_m(l) // 8 + 1 for l in levels)
+        pass_s = t32 / passes32
+        hbm_peak32, _ = peaks()
+        f32 = {"glups": sw32 * npts / t32 / 1e9, "sweeps": sw32, "seconds": t32,
+               "temporal_depth": 8,
+               "hbm_per_pass_gbs": 12.0 * npts / pass_s / 1e9,
+               "hbm_per_pass_frac": 12.0 * npts / pass_s / 1e9 / hbm_peak32,
+               "effective_hbm_frac": 12.0 * sw32 * npts / t32 / 1e9 / hbm_peak32,
+               "rel_residual_after": float(rn32[-1] / rn32[0]) if len(rn32) else None,
+               "schedule": "levels 0..16 then 16 x20"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, sample = oracle_sample(float(os.environ.get("SRJ_ORACLE_SECONDS", "15")))
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        clocks = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 sweeps on an FP32-pair iterate; f64 outer residual/update",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [SIDE, SIDE],
+            "config": {"workload": WORKLOAD if side == SIDE else WORKLOAD.replace("4096x4096", "%dx%d" % (side, side)),
+                       "grid": [side, side],
                        "precision": "mixed (FP64 refinement, FP32-pair inner)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (u+f FP64 268 MB, inner working set 335 MB)"},
             "time_to_tol_s": ms_max / args.steps / 1e3,
             "sweeps_per_solve": sweeps / args.steps, "outer_per_solve": outer / args.steps,
             "converged": ok, "rel_residual_check": rel_check,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
-                         "kernel": "inner pass (FP32-pair iterate), per-pass device time over "
-                                   "the timed region", "peak_kind": peak_kind},
+            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                         "unit": "T FP32-instr/s", "frac": alu_achieved / alu_peak,
+                         "traffic": None,
+                         "kernel": "wave2d_kernel<FP32-pair> inner pass, %d ops/LUP, "
+                                   "%.2f sweeps/pass; per-pass time = timed device time / passes"
+                                   % (DF_OPS_PER_LUP, sweeps_per_pass),
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x median SM clock "
+                                      "%.0f MHz" % sm_mhz},
+            "roofline_hbm": {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                             "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                             "bytes_per_pass": bytes_per_pass},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * npts,
                     "d2h_bytes_per_step": 8 * npts},
             "gpu_launches": int(passes + 2 * outer + args.steps),
             "plain_fp64": fp64,
+            "fp32_sweeps": f32,
             "mixed_vs_plain_speedup": (fp64["time_to_tol_s"] / (ms_max / args.steps / 1e3))
             if fp64 else None,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
@@ -320,6 +383,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f32", action="store_true")
+    ap.add_argument("--depth", type=int, default=0, help="temporal depth of the inner pass (0: library)")
+    ap.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs only)")
     args = ap.parse_args()
     rank, world = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
     if args.impl == "reference":

@@ -15,6 +15,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -61,6 +62,10 @@ struct srj_handle {
     // dense device staging for srj_solve_host
     void *dF = nullptr, *dU = nullptr;
     // graph of the device-driven cycle loop
+    bool host_loop = false;  // SRJ_LAUNCH=host: passes launched by a host loop
+    bool use_wave = false;   // 2D constant coefficients: temporally blocked passes
+    Wave2dPlan wplan{};
+    int num_sms = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -146,9 +151,37 @@ srj_status build_graph(srj_handle *h) {
     PassLaunch a = make_launch(h, true);
     a.cfg.use_cond = 1;
     a.cfg.cond = cond;
-    CK(add_generic_pass_node(h->kprec, h->vark, a, body));
+    if (h->use_wave) {
+        CK(wave2d_prepare(h->kprec, h->wplan.T));
+        CK(add_wave2d_node(h->wplan, a, body));
+    } else {
+        CK(add_generic_pass_node(h->kprec, h->vark, a, body));
+    }
     CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
     return SRJ_OK;
+}
+
+// Run the device-driven cycle loop until the solve state leaves RUNNING.
+// Default: one launch of the graph (conditional WHILE around the pass kernel).
+// With SRJ_LAUNCH=host (profilers cannot see kernels inside conditional
+// graphs) the same pass kernel is launched directly in batches of 64 and the
+// state is polled after each batch; passes issued after the end exit at once.
+srj_status run_loop(srj_handle *h) {
+    if (!h->host_loop) {
+        CK(cudaGraphLaunch(h->exec, h->stream));
+        return SRJ_OK;
+    }
+    PassLaunch a = make_launch(h, true);
+    for (;;) {
+        for (int i = 0; i < 64; ++i) {
+            if (h->use_wave) CK(wave2d_launch(h->wplan, a, h->stream));
+            else CK(generic_pass_launch(h->kprec, h->vark, a, h->stream));
+        }
+        DevState *probe = h->h_st;
+        CK(cudaMemcpyAsync(probe, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (probe->status != DST_RUNNING) return SRJ_OK;
+    }
 }
 
 void init_state(srj_handle *h, DevState &s, double tol, int tol_kind, int selector,
@@ -190,7 +223,8 @@ srj_status solve_plain(srj_handle *h, const void *f, void *u, double tol, int se
     init_state(h, *h->h_st, tol, h->opts.tol_kind, selector, level0, h->opts.max_sweeps, 0,
                nsched, 0);
     CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
-    CK(cudaGraphLaunch(h->exec, st));
+    s = run_loop(h);
+    if (s != SRJ_OK) return s;
     void *pads[2] = {h->U[0], h->U[1]};
     CK(copy_out_launch(h->kprec, h->geo, h->st, pads, u, st));
     CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
@@ -282,7 +316,8 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
         init_state(h, *h->h_st, h->opts.inner_tol, SRJ_TOL_REL, h->opts.selector, level,
                    inner_cap, 1, 0, trace_base);
         CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
-        CK(cudaGraphLaunch(h->exec, st));
+        s = run_loop(h);
+        if (s != SRJ_OK) return s;
         CK(outer_update_launch(oa, st));
         CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
         outer += 1;
@@ -414,7 +449,24 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
         ALLOC(h->invd32, h->padded * 4);
     }
     ALLOC(h->st, sizeof(DevState));
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) !=
+                cudaSuccess ||
+            h->num_sms <= 0)
+            h->num_sms = 152;
+    }
+    h->use_wave = (g.dim == 2) && !h->vark;
+    {
+        const char *lm = std::getenv("SRJ_LAUNCH");
+        h->host_loop = lm && std::strcmp(lm, "host") == 0;
+    }
     h->partials_cap = generic_partials_needed(g);
+    if (h->use_wave) {
+        h->wplan = wave2d_plan(h->kprec, wave2d_depth(h->kprec, o.temporal_depth), g, h->num_sms);
+        if (h->wplan.grid > h->partials_cap) h->partials_cap = h->wplan.grid;
+    }
     ALLOC(h->partials, (size_t)h->partials_cap * sizeof(double));
     h->trace_cap = o.trace_capacity > 0 ? o.trace_capacity : 1;
     ALLOC(h->trace_level, (size_t)h->trace_cap * sizeof(int32_t));

@@ -135,6 +135,20 @@ cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a,
 cudaError_t add_generic_pass_node(int prec, bool vark, const PassLaunch &a,
                                   cudaGraph_t body);
 
+// Temporally blocked 2D constant-coefficient pass (kernels_wave2d.cu).
+struct Wave2dPlan {
+    int T;        // sweeps fused per pass
+    void *entry;  // __global__ entry
+    int smem;     // dynamic shared memory bytes
+    int block, grid;
+    int nstrips, nsegs, R, nitems;
+};
+int wave2d_depth(int prec, int requested);
+Wave2dPlan wave2d_plan(int prec, int T, const GridGeo &g, int num_sms);
+cudaError_t wave2d_prepare(int prec, int T);
+cudaError_t wave2d_launch(const Wave2dPlan &p, const PassLaunch &a, cudaStream_t s);
+cudaError_t add_wave2d_node(const Wave2dPlan &p, const PassLaunch &a, cudaGraph_t body);
+
 // Whole-grid helpers (kernels_generic.cu).
 // FP64 outer residual of the mixed-precision path on dense user arrays:
 // writes r into the padded FP32 inner right-hand side, ||r||^2 partials and a

@@ -1,0 +1,128 @@
+// stencil_point.cuh -- per-point arithmetic of the relaxed Jacobi sweep
+// (Sec. 2, Eq. relaxed-jacobi) and of the residual, for the three state
+// representations: FP64, FP32 and the FP32 pair (df32.cuh).  Shared by the
+// pass kernels (file-local copies per translation unit).
+#pragma once
+
+#include "df32.cuh"
+#include "srj_internal.h"
+
+namespace srj {
+namespace {
+
+// ------------------------------------------------------------- element access
+template <int PREC>
+struct Elem;
+template <>
+struct Elem<PREC_F64> {
+    using T = double;   // state
+    using C = double;   // coefficients / rhs
+};
+template <>
+struct Elem<PREC_F32> {
+    using T = float;
+    using C = float;
+};
+template <>
+struct Elem<PREC_DF> {
+    using T = df32;
+    using C = float;
+};
+
+template <int PREC>
+__device__ __forceinline__ typename Elem<PREC>::T load_u(const IterBufs &b, int which,
+                                                        long long i) {
+    if constexpr (PREC == PREC_DF) {
+        const float *hi = (const float *)b.u[which];
+        const float *lo = (const float *)b.ulo[which];
+        return df32{hi[i], lo[i]};
+    } else {
+        return ((const typename Elem<PREC>::T *)b.u[which])[i];
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_u(const IterBufs &b, int which, long long i,
+                                        typename Elem<PREC>::T v) {
+    if constexpr (PREC == PREC_DF) {
+        ((float *)b.u[which])[i] = v.hi;
+        ((float *)b.ulo[which])[i] = v.lo;
+    } else {
+        ((typename Elem<PREC>::T *)b.u[which])[i] = v;
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ typename Elem<PREC>::T zero_u() {
+    if constexpr (PREC == PREC_DF) return df32{0.f, 0.f};
+    else return typename Elem<PREC>::T(0);
+}
+
+// ---------------------------------------------- relaxation, residual at a point
+// Neighbour values nb[0..5] = -x, +x, -y, +y, -z, +z (zero outside);
+// weights wgt[0..5] the matching face weights (variable k) or the axis
+// coefficients c_a (constant); invd = 1/D; f the right-hand side.
+//
+// SWEEP:  t = D^-1 (f + sum_q w_q u_q) - u_c;  u' = u_c + omega t
+// RESID:  r = D t
+template <int PREC, int DIM>
+struct Point {
+    using T = typename Elem<PREC>::T;
+    using C = typename Elem<PREC>::C;
+
+    // t = D^-1 (f + sum w u_nb) - u_c
+    __device__ __forceinline__ static T t_of(const T *nb, const C *wgt, C invd, C f,
+                                             T uc) {
+        if constexpr (PREC == PREC_DF) {
+            df32 s = df_mul_f(nb[0], wgt[0]);
+            s = df_add(s, df_mul_f(nb[1], wgt[1]));
+            if (DIM > 1) {
+                s = df_add(s, df_mul_f(nb[2], wgt[2]));
+                s = df_add(s, df_mul_f(nb[3], wgt[3]));
+            }
+            if (DIM > 2) {
+                s = df_add(s, df_mul_f(nb[4], wgt[4]));
+                s = df_add(s, df_mul_f(nb[5], wgt[5]));
+            }
+            s = df_add_f(s, f);
+            return df_sub(df_mul_f(s, invd), uc);
+        } else {
+            T s = f + wgt[0] * nb[0] + wgt[1] * nb[1];
+            if (DIM > 1) s += wgt[2] * nb[2] + wgt[3] * nb[3];
+            if (DIM > 2) s += wgt[4] * nb[4] + wgt[5] * nb[5];
+            return s * invd - uc;
+        }
+    }
+
+    // constant coefficients: t = a_x (u_-x + u_+x) + ... + D^-1 f - u_c with
+    // a = c / D, written as the cheaper sum-then-scale form.
+    __device__ __forceinline__ static T t_const(const T *nb, const C *a, C invd, C f, T uc) {
+        if constexpr (PREC == PREC_DF) {
+            df32 s = df_mul_f(df_add(nb[0], nb[1]), a[0]);
+            if (DIM > 1) s = df_add(s, df_mul_f(df_add(nb[2], nb[3]), a[1]));
+            if (DIM > 2) s = df_add(s, df_mul_f(df_add(nb[4], nb[5]), a[2]));
+            s = df_add(s, df_two_prod(invd, f));
+            return df_sub(s, uc);
+        } else {
+            T s = a[0] * (nb[0] + nb[1]);
+            if (DIM > 1) s += a[1] * (nb[2] + nb[3]);
+            if (DIM > 2) s += a[2] * (nb[4] + nb[5]);
+            return s + invd * f - uc;
+        }
+    }
+
+    __device__ __forceinline__ static T relax(T uc, T t, double omega) {
+        if constexpr (PREC == PREC_DF) return df_add(uc, df_mul_f(t, (float)omega));
+        else return uc + (C)omega * t;
+    }
+
+    __device__ __forceinline__ static double resid2(T t, C diag) {
+        double r;
+        if constexpr (PREC == PREC_DF) r = (double)diag * df_to_double(t);
+        else r = (double)(diag * t);
+        return r * r;
+    }
+};
+
+}  // namespace
+}  // namespace srj

@@ -2,7 +2,10 @@
 on the same seeded inputs.
 
 Tolerances:
- * FP64 -- relative 1e-10 on the solution and per-cycle residual norms, and
+ * FP64 -- relative 1e-10 on the solution; per-cycle residual norms within
+   1e-10 relative plus 1e-13 ||r0|| absolute (evaluating f - A u for an
+   iterate near the solution loses about eps64 ||f|| to cancellation, so a
+   tiny late-cycle norm cannot be compared purely relatively); and
    identical level sequences (a decision may differ only where the oracle's
    ratio lies within 1e-9 of a threshold 0.2 / 0.4; the tests check there is
    no such near-tie instead of skipping).
@@ -96,8 +99,9 @@ def test_residual_norm_f64(S, orc, name, n, eps, kind):
     f, k = case_inputs(name, n, kind)
     u = np.random.default_rng(5).standard_normal(f.size)
     h, kt = make(S, n, S.SRJ_PREC_F64, eps=eps, k=k)
+    fd, ud = dev(f), dev(u)
     try:
-        got = S.srj_residual_norm(h, dev(f).data_ptr(), dev(u).data_ptr())
+        got = S.srj_residual_norm(h, fd.data_ptr(), ud.data_ptr())
     finally:
         S.srj_destroy(h)
     ref = orc.residual_norm(orc.Problem(n, eps=eps, k=k), u, f)
@@ -111,15 +115,16 @@ def test_fixed_schedule_f64(S, orc, name, n, eps, kind):
     levels = [0, 1, 2, 3, 5, 8, 11, 9, 13]
     u0 = np.zeros(f.size)
     h, kt = make(S, n, S.SRJ_PREC_F64, eps=eps, k=k)
+    fd, ud = dev(f), dev(u0)
     try:
-        ud = dev(u0)
-        rn = S.srj_run_levels(h, dev(f).data_ptr(), ud.data_ptr(), levels)
+        rn = S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
         ug = ud.cpu().numpy()
     finally:
         S.srj_destroy(h)
     uo, rno = orc.run_levels(orc.Problem(n, eps=eps, k=k), f, u0, levels)
     assert np.max(np.abs(ug - uo)) <= 1e-10 * np.max(np.abs(uo))
-    assert np.max(np.abs(rn - rno) / rno) <= 1e-10
+    r0 = orc.residual_norm(orc.Problem(n, eps=eps, k=k), u0, f)
+    assert np.all(np.abs(rn - rno) <= 1e-10 * rno + 1e-13 * r0)
 
 
 @pytest.mark.parametrize("name,n,eps,kind", CASES, ids=[c[0] for c in CASES])
@@ -131,9 +136,9 @@ def test_heuristic_solve_f64(S, orc, name, n, eps, kind):
     ref = orc.srj_solve(P, f, tol=1e-8)
     assert not near_tie(ref["rns"], ref["r0"])
     h, kt = make(S, n, S.SRJ_PREC_F64, eps=eps, k=k)
+    fd, ud = dev(f), dev(np.zeros(f.size))
     try:
-        ud = dev(np.zeros(f.size))
-        st = S.srj_solve(h, dev(f).data_ptr(), ud.data_ptr(), 1e-8)
+        st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-8)
         lv, rn = S.srj_get_trace(h)
         ug = ud.cpu().numpy()
     finally:
@@ -141,7 +146,7 @@ def test_heuristic_solve_f64(S, orc, name, n, eps, kind):
     assert st["status"] == S.SRJ_OK
     assert st["sweeps"] == ref["sweeps"] and st["cycles"] == ref["cycles"]
     assert list(lv) == list(ref["levels"])
-    assert np.max(np.abs(rn - ref["rns"]) / ref["rns"]) <= 1e-10
+    assert np.all(np.abs(rn - ref["rns"]) <= 1e-10 * ref["rns"] + 1e-13 * ref["r0"])
     assert np.max(np.abs(ug - ref["u"])) <= 1e-10 * np.max(np.abs(ref["u"]))
 
 
@@ -154,8 +159,9 @@ def test_paper_n100_pattern_on_gpu(S, orc):
     for rule, sel in (("heuristic", S.SRJ_SEL_HEURISTIC), ("increasing", S.SRJ_SEL_INCREASING)):
         ref = orc.srj_solve(orc.Problem([N]), f, tol=1e-7, tol_kind="abs", rule=rule)
         h, _ = make(S, [N], S.SRJ_PREC_F64, selector=sel, tol_kind=S.SRJ_TOL_ABS)
+        fd, ud = dev(f), dev(np.zeros(N))
         try:
-            st = S.srj_solve(h, dev(f).data_ptr(), dev(np.zeros(N)).data_ptr(), 1e-7)
+            st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-7)
             lv, _ = S.srj_get_trace(h)
         finally:
             S.srj_destroy(h)
@@ -169,9 +175,9 @@ def test_fixed_schedule_f32_within_bound(S, orc, name, n, eps, kind):
     f, k = case_inputs(name, n, kind)
     levels = [0, 1, 2, 3, 4, 6, 8]
     h, _ = make(S, n, S.SRJ_PREC_F32, eps=eps)
+    fd, ud = dev(f, torch.float32), dev(np.zeros(f.size), torch.float32)
     try:
-        ud = dev(np.zeros(f.size), torch.float32)
-        S.srj_run_levels(h, dev(f, torch.float32).data_ptr(), ud.data_ptr(), levels)
+        S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
         ug = ud.cpu().numpy().astype(np.float64)
     finally:
         S.srj_destroy(h)
@@ -189,9 +195,9 @@ def test_mixed_precision_solve(S, orc, name, n, eps, kind):
     P = orc.Problem(n, eps=eps, k=k)
     ref = orc.srj_solve(P, f, tol=1e-8)
     h, kt = make(S, n, S.SRJ_PREC_MIXED, eps=eps, k=k)
+    fd, ud = dev(f), dev(np.zeros(f.size))
     try:
-        ud = dev(np.zeros(f.size))
-        st = S.srj_solve(h, dev(f).data_ptr(), ud.data_ptr(), 1e-8)
+        st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-8)
         ug = ud.cpu().numpy()
     finally:
         S.srj_destroy(h)
@@ -207,9 +213,9 @@ def test_solve_host_matches_device(S):
     n = [96, 80]
     f = inputs.uniform_rhs(n, seed=9).ravel()
     h, _ = make(S, n, S.SRJ_PREC_F64)
+    fd, ud = dev(f), dev(np.zeros(f.size))
     try:
-        ud = dev(np.zeros(f.size))
-        a = S.srj_solve(h, dev(f).data_ptr(), ud.data_ptr(), 1e-8)
+        a = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-8)
         fh = torch.as_tensor(f).pin_memory()
         uh = torch.zeros(f.size, dtype=torch.float64).pin_memory()
         b = S.srj_solve_host(h, fh.data_ptr(), uh.data_ptr(), 1e-8)
@@ -239,9 +245,124 @@ def test_notconv_status_and_cap(S):
     n = [256]
     f = np.ones(256)
     h, _ = make(S, n, S.SRJ_PREC_F64, max_sweeps=50)
+    fd, ud = dev(f), dev(np.zeros(256))
     try:
-        st = S.srj_solve(h, dev(f).data_ptr(), dev(np.zeros(256)).data_ptr(), 1e-12)
+        st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-12)
     finally:
         S.srj_destroy(h)
     assert st["status"] == S.SRJ_ENOTCONV
     assert 50 <= st["sweeps"] < 50 + 2362
+
+
+# ------------------------------------------- temporally blocked 2D passes
+WAVE_GRIDS = [[250, 131], [33, 70], [112, 300], [500, 17]]
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+@pytest.mark.parametrize("n", WAVE_GRIDS, ids=lambda n: "x".join(map(str, n)))
+def test_wave_f64_fixed_schedule(S, orc, n, depth):
+    f = inputs.uniform_rhs(n, seed=11).ravel()
+    levels = [0, 1, 2, 3, 4, 6, 9, 12]
+    h, _ = make(S, n, S.SRJ_PREC_F64, eps=[0.3, 1.0], temporal_depth=depth)
+    fd, ud = dev(f), dev(np.zeros(f.size))
+    try:
+        rn = S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    P = orc.Problem(n, eps=[0.3, 1.0])
+    uo, rno = orc.run_levels(P, f, np.zeros(f.size), levels)
+    r0 = orc.residual_norm(P, np.zeros(f.size), f)
+    assert np.max(np.abs(ug - uo)) <= 1e-10 * np.max(np.abs(uo))
+    assert np.all(np.abs(rn - rno) <= 1e-10 * rno + 1e-13 * r0)
+
+
+@pytest.mark.parametrize("depth", [4, 8])
+@pytest.mark.parametrize("n", WAVE_GRIDS, ids=lambda n: "x".join(map(str, n)))
+def test_wave_f32_fixed_schedule_within_bound(S, orc, n, depth):
+    f = inputs.uniform_rhs(n, seed=12).ravel()
+    levels = [0, 1, 2, 3, 5, 7, 8]
+    h, _ = make(S, n, S.SRJ_PREC_F32, temporal_depth=depth)
+    fd, ud = dev(f, torch.float32), dev(np.zeros(f.size), torch.float32)
+    try:
+        rn = S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
+        ug = ud.cpu().numpy().astype(np.float64)
+    finally:
+        S.srj_destroy(h)
+    f32 = f.astype(np.float32).astype(np.float64)
+    P = orc.Problem(n)
+    uo, rno = orc.run_levels(P, f32, np.zeros(f.size), levels)
+    bound = 8 * EPS32 * sum(S.srj_level_m(l) ** 3 for l in levels) * np.max(np.abs(uo))
+    assert np.max(np.abs(ug - uo)) <= bound
+    r0 = orc.residual_norm(P, np.zeros(f.size), f32)
+    assert np.all(np.abs(rn - rno) <= 1e-3 * rno + 1e-5 * r0)
+
+
+@pytest.mark.parametrize("depth", [2, 4])
+@pytest.mark.parametrize("n", WAVE_GRIDS, ids=lambda n: "x".join(map(str, n)))
+def test_wave_mixed_solve(S, orc, n, depth):
+    f = inputs.uniform_rhs(n, seed=13).ravel()
+    P = orc.Problem(n, eps=[1.0, 0.2])
+    ref = orc.srj_solve(P, f, tol=1e-8)
+    h, _ = make(S, n, S.SRJ_PREC_MIXED, eps=[1.0, 0.2], temporal_depth=depth)
+    fd, ud = dev(f), dev(np.zeros(f.size))
+    try:
+        st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-8)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    assert st["status"] == S.SRJ_OK, st
+    rn_true = orc.residual_norm(P, ug, f)
+    assert rn_true / ref["r0"] < 1e-8
+    lam = lam_min_const(n, [1.0, 0.2])
+    assert np.linalg.norm(ug - ref["u"]) <= (rn_true + ref["rn"]) / lam * (1 + 1e-6)
+    # Sweep count bounded against the FP64 oracle's: each refinement step
+    # restarts its inner solve a few levels lower and climbs again, which costs
+    # at most about two extra cycles per step at the top level (<= 2 x 2362).
+    assert st["sweeps"] <= ref["sweeps"] + st["outer"] * 2 * 2362
+
+
+# ------------------------------------------------ full size (bench config)
+def _torch_rel_residual(u, f, side):
+    uu = u.view(side, side)
+    ff = f.view(side, side)
+    up = torch.nn.functional.pad(uu, (1, 1, 1, 1))
+    Au = float((side + 1) ** 2) * (4 * uu - up[1:-1, :-2] - up[1:-1, 2:] - up[:-2, 1:-1]
+                                   - up[2:, 1:-1])
+    return float(torch.linalg.norm(ff - Au) / torch.linalg.norm(ff))
+
+
+def test_full_size_4096_f64_schedule_elementwise(S, orc):
+    """4096^2, the bench's grid: a fixed schedule of short cycles, every
+    element against the oracle (which runs the same sweeps on the CPU)."""
+    n = [4096, 4096]
+    f = inputs.uniform_rhs(n, seed=0).ravel()
+    levels = [0, 1, 2, 3]
+    h, _ = make(S, n, S.SRJ_PREC_F64)
+    fd, ud = dev(f), dev(np.zeros(f.size))
+    try:
+        rn = S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    P = orc.Problem(n)
+    uo, rno = orc.run_levels(P, f, np.zeros(f.size), levels)
+    assert np.max(np.abs(ug - uo)) <= 1e-12 * np.max(np.abs(uo))
+    assert np.all(np.abs(rn - rno) <= 1e-10 * rno)
+
+
+def test_full_size_4096_mixed_solve_residual(S):
+    """The bench's solve (mixed precision, 4096^2, rel 1e-8): the relative
+    residual recomputed independently in FP64 from the returned solution."""
+    n = [4096, 4096]
+    f = inputs.uniform_rhs(n, seed=0).ravel()
+    h, _ = make(S, n, S.SRJ_PREC_MIXED)
+    fd, ud = dev(f), dev(np.zeros(f.size))
+    try:
+        st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-8)
+    finally:
+        S.srj_destroy(h)
+    assert st["status"] == S.SRJ_OK, st
+    rel = _torch_rel_residual(ud, fd, 4096)
+    assert rel < 1e-8
+    assert abs(st["rn"] / st["r0"] - rel) <= 1e-3 * rel
