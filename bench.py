@@ -32,10 +32,12 @@ UNIT = "GLUP/s"
 SIDE = 4096
 TOL = 1e-8
 # FP32 instructions per grid-point update of the FP32-pair relaxation (2D,
-# constant coefficients): 4 compensated adds (11 each), 2 compensated scalings
-# (6 each), the exact product D^-1 f (2), the compensated subtraction of u (11)
-# and the update u + omega t (6 + 11).
-DF_OPS_PER_LUP = 86
+# constant coefficients; df_t2d + df_axpy in csrc/df32.cuh): five Knuth
+# two-sums (6 each), four FMA two-products (2 each) with two low-part FMAs, ten
+# plain low-part adds, one Dekker renormalisation (3) for t; then one
+# two-product, one FMA, one two-sum, two adds and one renormalisation for
+# u + omega t.
+DF_OPS_PER_LUP = 65
 WORKLOAD = ("2D Poisson 5-point, 4096x4096 interior, zero Dirichlet, f~U[-1,1] (seed 0+rank), "
             "u0=0, rel residual 1e-8, SRJ scheme family + Alg. 1 heuristic")
 
@@ -200,6 +202,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched
+def batched_leg(srj, inputs, torch, stream, seed=0, count=256, fp64=True):
+    """256 independent 2D problems (sides U{64..1024}, half anisotropic), f ~
+    N(0,1), rel 1e-8: one batched mixed-precision solve (persistent kernel in
+    a CUDA graph, autotuned depth/segment), against plain FP64 SRJ with Alg. 1
+    solving the same problems one after another on the same GPU."""
+    probs = inputs.batched_problems(count=count, seed=seed)
+    ns = [p["n"] for p in probs]
+    eps = [p["eps"] for p in probs]
+    fs = [torch.as_tensor(inputs.normal_rhs(p["n"], seed=p["seed_f"]).ravel(), device="cuda")
+          for p in probs]
+    us = [torch.zeros_like(f) for f in fs]
+    npts = [f.numel() for f in fs]
+    h = srj.srj_create_batched(ns, eps=eps, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    rc, st = srj.srj_solve_batched(h, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], TOL)
+    tune_s = time.perf_counter() - t0  # first call includes the autotuner
+    for u in us:
+        u.zero_()
+    rc, st = srj.srj_solve_batched(h, [f.data_ptr() for f in fs], [u.data_ptr() for u in us], TOL)
+    srj.srj_destroy(h)
+    secs = st[0]["seconds"]
+    lups = sum(s["sweeps"] * n for s, n in zip(st, npts))
+    out = {"problems": count, "points": sum(npts), "converged": rc == srj.SRJ_OK,
+           "time_to_tol_s": secs, "glups": lups / secs / 1e9,
+           "sweeps_total": sum(s["sweeps"] for s in st), "first_call_with_autotune_s": tune_s}
+    if fp64:
+        tot, sw64, ok = 0.0, 0, True
+        for p, f in zip(probs, fs):
+            h64 = srj.srj_create(p["n"], eps=p["eps"], precision=srj.SRJ_PREC_F64,
+                                 stream=stream.cuda_stream)
+            u = torch.zeros_like(f)
+            s64 = srj.srj_solve(h64, f.data_ptr(), u.data_ptr(), TOL)
+            srj.srj_destroy(h64)
+            tot += s64["seconds"]
+            sw64 += s64["sweeps"]
+            ok = ok and s64["status"] == srj.SRJ_OK
+        out["plain_fp64_sequential"] = {"time_to_tol_s": tot, "sweeps_total": sw64, "converged": ok}
+        out["speedup_vs_plain_fp64"] = tot / secs
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import numpy as np
@@ -330,6 +374,10 @@ def run_ours(args, rank, world):
                "rel_residual_after": float(rn32[-1] / rn32[0]) if len(rn32) else None,
                "schedule": "levels 0..16 then 16 x20"}
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(srj, inputs, torch, stream, seed=rank, fp64=not args.no_fp64)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, sample = oracle_sample(float(os.environ.get("SRJ_ORACLE_SECONDS", "15")))
@@ -367,6 +415,7 @@ def run_ours(args, rank, world):
             "gpu_launches": int(passes + 2 * outer + args.steps),
             "plain_fp64": fp64,
             "fp32_sweeps": f32,
+            "batched": batched,
             "mixed_vs_plain_speedup": (fp64["time_to_tol_s"] / (ms_max / args.steps / 1e3))
             if fp64 else None,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
@@ -385,6 +434,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f32", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--depth", type=int, default=0, help="temporal depth of the inner pass (0: library)")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs only)")
     args = ap.parse_args()

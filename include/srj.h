@@ -176,6 +176,61 @@ srj_status srj_residual_norm(srj_handle *h, const void *f, const void *u,
 int64_t srj_get_trace(const srj_handle *h, int32_t *levels, double *rn,
                       int64_t capacity);
 
+/* Batched solver: nprob independent 2D constant-coefficient problems of any
+ * sizes (grids[i], stencils[i] with k == NULL; stencils may be NULL), solved
+ * together in mixed precision (opts->precision must be SRJ_PREC_MIXED): one
+ * persistent kernel advances every unfinished problem by one step of its own
+ * solve (FP64 residual, inner SRJ pass, FP64 update) per launch, inside one
+ * CUDA graph.  grids, stencils: HOST arrays of nprob structs; opts shared by
+ * all problems.  The temporal depth (opts->temporal_depth == 0) and the
+ * segment height of the persistent kernel are chosen by timing candidates on
+ * the first solve (cached in the file named by the environment variable
+ * SRJ_AUTOTUNE_CACHE when set).  Workspace: about 20 bytes per grid point
+ * plus per-item scratch.  Returns SRJ_EUNSUPPORTED for 1D/3D grids or
+ * variable coefficients. */
+srj_status srj_create_batched(int32_t nprob, const srj_grid *grids,
+                              const srj_stencil *stencils, const srj_opts *opts,
+                              void *stream, srj_handle **out);
+
+/* Solve every problem of a batched handle to tol (kind from opts).  f and u
+ * are HOST arrays of nprob DEVICE pointers to dense FP64 arrays (f[i], u[i]
+ * sized like grids[i]); u[i] holds u0 on entry and the solution on exit.
+ * stats: HOST array of nprob srj_stats (may be NULL); stats[i].seconds is the
+ * device time of the whole batch.  Returns SRJ_OK if every problem converged,
+ * else the first non-OK status. */
+srj_status srj_solve_batched(srj_handle *h, const double *const *f, double *const *u,
+                             double tol, srj_stats *stats);
+
+/* Learned scheme selector (SRJ_SEL_MLP; not in the paper, which selects
+ * with Alg. 1).  A network 12 -> 64 -> 64 -> 25 (ReLU) maps the solver state
+ * -- log of the last 8 residual ratios, log10 of the grid size, dimension and
+ * the current level -- to the level of the next cycle; Alg. 1 takes over for
+ * the next decision whenever a picked cycle did not shrink the residual.
+ * Parameters: 6617 values W1 (64x12), b1, W2 (64x64), b2, W3 (25x64), b3,
+ * row-major, as BF16 bit patterns.
+ *
+ * srj_mlp_set_weights: copy the BF16 weights (HOST array of count == 6617)
+ * into h (single-grid or batched); required before a solve with SRJ_SEL_MLP. */
+srj_status srj_mlp_set_weights(srj_handle *h, const uint16_t *w, int64_t count);
+
+/* Evaluate the selector network on the GPU for n feature rows (HOST arrays:
+ * w 6617 BF16, x n*12 floats); writes the argmax level of each row into
+ * pick_host (n ints) and, if not NULL, the 25 FP32 logits per row into
+ * logits_host.  Uses the current device; allocates and frees its scratch. */
+srj_status srj_mlp_forward(const uint16_t *w_host, const float *x_host, int64_t n,
+                           int32_t *pick_host, float *logits_host);
+
+/* Train the selector on the GPU: `steps` Adam steps (beta 0.9 / 0.999, eps
+ * 1e-8, learning rate lr, moments starting at zero) of mean softmax
+ * cross-entropy over minibatches of `batch` (<= 64) samples.  DEVICE arrays:
+ * x_dev (n x 12 floats), y_dev (n labels in [0, 25)), order_dev (steps*batch
+ * sample indices, the minibatch order), theta_dev (6617 FP32 parameters, in:
+ * initial, out: trained).  loss_host (HOST, steps floats, may be NULL)
+ * receives the minibatch losses.  Runs on `stream` and synchronises it. */
+srj_status srj_mlp_train(const float *x_dev, const int32_t *y_dev, int64_t n,
+                         const int32_t *order_dev, int64_t steps, int32_t batch, float lr,
+                         float *theta_dev, float *loss_host, void *stream);
+
 /* Text describing the last failure on h (static storage inside h), or a
  * generic text for h == NULL. */
 const char *srj_last_error(const srj_handle *h);

@@ -71,6 +71,30 @@ struct srj_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long last_cycles = 0;
     std::string err;
+    struct BatchData *batch = nullptr;  // srj_create_batched handles only
+    uint16_t *mlp_w = nullptr;          // learned selector weights (BF16, 6617)
+    bool mlp_loaded = false;
+};
+
+// Workspace and schedule of a batched handle.
+struct BatchData {
+    int nprob = 0;
+    std::vector<BatchProb> probs;  // host copy of the descriptors
+    std::vector<long long> npts;
+    BatchProb *dprobs = nullptr;
+    BatchState *dstates = nullptr;
+    BatchState *hstates = nullptr;  // pinned
+    int32_t *item_prob = nullptr;
+    double *partials = nullptr;
+    int items_cap = 0;
+    unsigned int *ndone = nullptr;
+    float *arena = nullptr;  // all inner buffers: per problem r32, hi0, hi1, lo0, lo1
+    size_t arena_floats = 0;
+    int T = 4, R = 64, total_items = 0;
+    bool tuned = false;
+    double graph_tol = -1.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -126,7 +150,7 @@ PassLaunch make_launch(srj_handle *h, bool inner) {
     a.cfg.trace_rn = h->trace_rn;
     a.cfg.trace_cap = h->trace_cap;
     a.cfg.use_cond = 0;
-    a.cfg.mlp_w = nullptr;
+    a.cfg.mlp_w = h->mlp_w;
     for (int l = 0; l < kNumLevels; ++l) {
         a.lvl_m[l] = kLevelM[l];
         a.lvl_off[l] = level_offset(l);
@@ -198,6 +222,8 @@ void init_state(srj_handle *h, DevState &s, double tol, int tol_kind, int select
     s.level = level0;
     s.trace_base = trace_base;
     s.status = DST_RUNNING;
+    s.dim = h->geo.dim;
+    s.npoints = (double)h->npts;
 }
 
 srj_status status_of(int dst) {
@@ -336,6 +362,204 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
     return status_of(result);
 }
 
+// ------------------------------------------------------------------ batched
+// Item tables for temporal depth T and segment height R (problem-major).
+srj_status batch_layout(srj_handle *h, int T, int R) {
+    BatchData *B = h->batch;
+    const int outw = batched_outw(T);
+    std::vector<int32_t> owner;
+    int base = 0;
+    for (int p = 0; p < B->nprob; ++p) {
+        BatchProb &P = B->probs[p];
+        P.nstrips = (P.geo.nx + outw - 1) / outw;
+        P.R = R < P.geo.ny ? R : P.geo.ny;
+        P.nsegs = (P.geo.ny + P.R - 1) / P.R;
+        P.nitems = P.nstrips * P.nsegs;
+        P.item_base = base;
+        for (int i = 0; i < P.nitems; ++i) owner.push_back(p);
+        base += P.nitems;
+    }
+    B->total_items = base;
+    B->T = T;
+    B->R = R;
+    if (base > B->items_cap) {
+        dfree(B->item_prob);
+        dfree(B->partials);
+        B->item_prob = nullptr;
+        B->partials = nullptr;
+        if (dalloc(&B->item_prob, (size_t)base * sizeof(int32_t)) != cudaSuccess ||
+            dalloc(&B->partials, (size_t)base * sizeof(double)) != cudaSuccess)
+            return fail(h, SRJ_ENOMEM, "batched item tables");
+        B->items_cap = base;
+    }
+    CK(cudaMemcpyAsync(B->item_prob, owner.data(), (size_t)base * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(B->dprobs, B->probs.data(), B->probs.size() * sizeof(BatchProb),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return SRJ_OK;
+}
+
+BatchLaunch batch_args(srj_handle *h, double tol, bool tuning) {
+    BatchData *B = h->batch;
+    BatchLaunch b{};
+    b.probs = B->dprobs;
+    b.states = B->dstates;
+    b.item_prob = B->item_prob;
+    b.partials = B->partials;
+    b.ndone = B->ndone;
+    b.nprob = B->nprob;
+    b.total_items = B->total_items;
+    b.w64 = h->w64;
+    for (int l = 0; l < kNumLevels; ++l) {
+        b.lvl_m[l] = kLevelM[l];
+        b.lvl_off[l] = level_offset(l);
+    }
+    b.tol = tol;
+    b.inner_tol = tuning ? -1.0 : h->opts.inner_tol;
+    b.max_sweeps = tuning ? (1LL << 60) : h->opts.max_sweeps;
+    b.max_outer = 200;
+    b.tol_kind = h->opts.tol_kind;
+    b.selector = h->opts.selector;
+    b.max_level = h->opts.max_level;
+    b.fixed_level = h->opts.fixed_level;
+    b.stall_stop = tuning ? 0 : 1;
+    b.cfg.trace_cap = 0;
+    b.cfg.mlp_w = h->mlp_w;
+    return b;
+}
+
+srj_status batch_reset(srj_handle *h) {
+    BatchData *B = h->batch;
+    for (int p = 0; p < B->nprob; ++p) {
+        BatchState &S = B->hstates[p];
+        std::memset(&S, 0, sizeof(S));
+        S.phase = 0;  // outer residual first
+        S.carry = h->opts.level0;
+        S.result = DST_RUNNING;
+    }
+    CK(cudaMemcpyAsync(B->dstates, B->hstates, (size_t)B->nprob * sizeof(BatchState),
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(B->ndone, 0, sizeof(unsigned int), h->stream));
+    CK(cudaMemsetAsync(B->arena, 0, B->arena_floats * sizeof(float), h->stream));
+    return SRJ_OK;
+}
+
+// Choose (T, R) by timing a window of batched launches on the real problems.
+// During tuning the inner solves never end (tolerance < 0, no stall stop), so
+// no UPDATE step runs and the caller's u is only read.
+srj_status batch_autotune(srj_handle *h) {
+    BatchData *B = h->batch;
+    std::string key;
+    {
+        char buf[64];
+        snprintf(buf, sizeof buf, "n%d", B->nprob);
+        key = buf;
+        unsigned long long hsh = 1469598103934665603ULL;
+        for (const BatchProb &P : B->probs) {
+            hsh = (hsh ^ (unsigned long long)P.geo.nx) * 1099511628211ULL;
+            hsh = (hsh ^ (unsigned long long)P.geo.ny) * 1099511628211ULL;
+        }
+        snprintf(buf, sizeof buf, "-%016llx", hsh);
+        key += buf;
+    }
+    const char *cache = std::getenv("SRJ_AUTOTUNE_CACHE");
+    if (cache) {
+        FILE *fp = std::fopen(cache, "r");
+        if (fp) {
+            char k[128];
+            int T, R;
+            while (std::fscanf(fp, "%127s %d %d", k, &T, &R) == 3) {
+                if (key == k) {
+                    std::fclose(fp);
+                    srj_status s = batch_layout(h, T, R);
+                    if (s == SRJ_OK) B->tuned = true;
+                    return s;
+                }
+            }
+            std::fclose(fp);
+        }
+    }
+    const int Ts[2] = {2, 4};
+    const int Rs[3] = {32, 64, 128};
+    double best = -1.0;
+    int bestT = 4, bestR = 64;
+    for (int T : Ts) {
+        if (h->opts.temporal_depth && T != h->opts.temporal_depth) continue;
+        CK(batched_prepare(T));
+        for (int R : Rs) {
+            srj_status s = batch_layout(h, T, R);
+            if (s != SRJ_OK) return s;
+            s = batch_reset(h);
+            if (s != SRJ_OK) return s;
+            BatchLaunch b = batch_args(h, 1e-300, true);
+            for (int i = 0; i < 4; ++i) CK(batched_launch(T, h->num_sms, b, h->stream));
+            CK(cudaMemcpyAsync(B->hstates, B->dstates, (size_t)B->nprob * sizeof(BatchState),
+                               cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            std::vector<long long> before(B->nprob);
+            for (int p = 0; p < B->nprob; ++p) before[p] = B->hstates[p].in.sweeps;
+            CK(cudaEventRecord(h->ev0, h->stream));
+            for (int i = 0; i < 12; ++i) CK(batched_launch(T, h->num_sms, b, h->stream));
+            CK(cudaEventRecord(h->ev1, h->stream));
+            CK(cudaMemcpyAsync(B->hstates, B->dstates, (size_t)B->nprob * sizeof(BatchState),
+                               cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+            double lups = 0.0;
+            for (int p = 0; p < B->nprob; ++p)
+                lups += (double)(B->hstates[p].in.sweeps - before[p]) * (double)B->npts[p];
+            const double rate = ms > 0 ? lups / ms : 0.0;
+            if (rate > best) {
+                best = rate;
+                bestT = T;
+                bestR = R;
+            }
+        }
+    }
+    srj_status s = batch_layout(h, bestT, bestR);
+    if (s != SRJ_OK) return s;
+    B->tuned = true;
+    if (cache) {
+        FILE *fp = std::fopen(cache, "a");
+        if (fp) {
+            std::fprintf(fp, "%s %d %d\n", key.c_str(), bestT, bestR);
+            std::fclose(fp);
+        }
+    }
+    return SRJ_OK;
+}
+
+srj_status batch_build_graph(srj_handle *h, double tol) {
+    BatchData *B = h->batch;
+    if (B->exec && B->graph_tol == tol) return SRJ_OK;
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        cudaGraphDestroy(B->graph);
+        B->exec = nullptr;
+        B->graph = nullptr;
+    }
+    CK(batched_prepare(B->T));
+    CK(cudaGraphCreate(&B->graph, 0));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, B->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, B->graph, nullptr, nullptr, 0, &np));
+    BatchLaunch b = batch_args(h, tol, false);
+    b.cfg.use_cond = 1;
+    b.cfg.cond = cond;
+    CK(add_batched_node(B->T, h->num_sms, b, np.conditional.phGraph_out[0]));
+    CK(cudaGraphInstantiate(&B->exec, B->graph, 0));
+    B->graph_tol = tol;
+    return SRJ_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -375,10 +599,6 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
         return SRJ_EINVAL;
     };
     if (o.selector < 0 || o.selector > SRJ_SEL_MLP) return bad("selector");
-    if (o.selector == SRJ_SEL_MLP) {
-        delete h;
-        return SRJ_EUNSUPPORTED;
-    }
     if (o.precision < 0 || o.precision > SRJ_PREC_MIXED) return bad("precision");
     if (o.tol_kind != SRJ_TOL_REL && o.tol_kind != SRJ_TOL_ABS) return bad("tol_kind");
     if (o.max_level < 0 || o.max_level > kMaxLevel) return bad("max_level");
@@ -449,6 +669,7 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
         ALLOC(h->invd32, h->padded * 4);
     }
     ALLOC(h->st, sizeof(DevState));
+    ALLOC(h->mlp_w, 6617 * sizeof(uint16_t));
     {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -523,6 +744,8 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
 
 srj_status srj_solve(srj_handle *h, const void *f, void *u, double tol, srj_stats *stats) {
     if (!h) return SRJ_EINVAL;
+    if (h->opts.selector == SRJ_SEL_MLP && !h->mlp_loaded)
+        return fail(h, SRJ_EINVAL, "srj_solve: learned selector without weights");
     if (!f || !u || !(tol > 0) || !std::isfinite(tol))
         return fail(h, SRJ_EINVAL, "srj_solve: null array or tol not a positive finite number");
     if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -544,6 +767,8 @@ srj_status srj_solve(srj_handle *h, const void *f, void *u, double tol, srj_stat
 srj_status srj_solve_host(srj_handle *h, const void *f_host, void *u_host, double tol,
                           srj_stats *stats) {
     if (!h) return SRJ_EINVAL;
+    if (h->opts.selector == SRJ_SEL_MLP && !h->mlp_loaded)
+        return fail(h, SRJ_EINVAL, "srj_solve_host: learned selector without weights");
     if (!f_host || !u_host) return fail(h, SRJ_EINVAL, "srj_solve_host: null array");
     const size_t bytes = (size_t)h->npts * h->esize;
     if (!h->dF) {
@@ -634,6 +859,156 @@ int64_t srj_get_trace(const srj_handle *h, int32_t *levels, double *rn, int64_t 
     return h->last_cycles;
 }
 
+srj_status srj_create_batched(int32_t nprob, const srj_grid *grids, const srj_stencil *stencils,
+                              const srj_opts *opts, void *stream, srj_handle **out) {
+    if (out) *out = nullptr;
+    if (!out || !grids || nprob < 1) return SRJ_EINVAL;
+    srj_opts o{};
+    if (opts) o = *opts;
+    if (o.precision != SRJ_PREC_MIXED) return SRJ_EUNSUPPORTED;
+    if (o.temporal_depth != 0 && o.temporal_depth != 2 && o.temporal_depth != 4)
+        return SRJ_EINVAL;
+    for (int p = 0; p < nprob; ++p) {
+        if (grids[p].dim != 2 || (stencils && stencils[p].k)) return SRJ_EUNSUPPORTED;
+        if (grids[p].n[0] < 1 || grids[p].n[1] < 1 || grids[p].n[0] > (1 << 20) ||
+            grids[p].n[1] > (1 << 20))
+            return SRJ_EINVAL;
+    }
+    // The scheme tables, options and events come from an ordinary handle on a
+    // 1x1 grid; the batch owns its own per-problem workspace.
+    srj_grid g1{};
+    g1.dim = 2;
+    g1.n[0] = g1.n[1] = 1;
+    srj_handle *h = nullptr;
+    srj_status s = srj_create(&g1, nullptr, &o, stream, &h);
+    if (s != SRJ_OK) return s;
+    BatchData *B = new (std::nothrow) BatchData();
+    if (!B) {
+        srj_destroy(h);
+        return SRJ_ENOMEM;
+    }
+    h->batch = B;
+    B->nprob = nprob;
+    B->probs.resize(nprob);
+    B->npts.resize(nprob);
+    size_t floats = 0;
+    std::vector<size_t> offs(nprob);
+    for (int p = 0; p < nprob; ++p) {
+        BatchProb &P = B->probs[p];
+        std::memset(&P, 0, sizeof(P));
+        GridGeo &g = P.geo;
+        g.dim = 2;
+        g.nx = (int)grids[p].n[0];
+        g.ny = (int)grids[p].n[1];
+        g.nz = 1;
+        const double hx = grids[p].h[0] > 0 ? grids[p].h[0] : 1.0 / (g.nx + 1.0);
+        const double hy = grids[p].h[1] > 0 ? grids[p].h[1] : 1.0 / (g.ny + 1.0);
+        const double ex = stencils && stencils[p].eps[0] > 0 ? stencils[p].eps[0] : 1.0;
+        const double ey = stencils && stencils[p].eps[1] > 0 ? stencils[p].eps[1] : 1.0;
+        g.cx = ex / (hx * hx);
+        g.cy = ey / (hy * hy);
+        g.cz = 0.0;
+        g.diag = 2.0 * (g.cx + g.cy);
+        g.pitch = ((long long)g.nx + 31) / 32 * 32;
+        g.plane = g.pitch * g.ny;
+        B->npts[p] = (long long)g.nx * g.ny;
+        offs[p] = floats;
+        floats += 5 * (size_t)g.plane;
+    }
+    B->arena_floats = floats;
+    if (dalloc(&B->arena, floats * sizeof(float)) != cudaSuccess ||
+        dalloc(&B->dprobs, (size_t)nprob * sizeof(BatchProb)) != cudaSuccess ||
+        dalloc(&B->dstates, (size_t)nprob * sizeof(BatchState)) != cudaSuccess ||
+        dalloc(&B->ndone, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMallocHost((void **)&B->hstates, (size_t)nprob * sizeof(BatchState)) != cudaSuccess) {
+        srj_destroy(h);
+        return SRJ_ENOMEM;
+    }
+    for (int p = 0; p < nprob; ++p) {
+        BatchProb &P = B->probs[p];
+        float *base = B->arena + offs[p];
+        const size_t pl = (size_t)P.geo.plane;
+        P.inner.f = base;
+        P.inner.u[0] = base + pl;
+        P.inner.u[1] = base + 2 * pl;
+        P.inner.ulo[0] = base + 3 * pl;
+        P.inner.ulo[1] = base + 4 * pl;
+    }
+    s = batch_layout(h, o.temporal_depth ? o.temporal_depth : 4, 64);
+    if (s == SRJ_OK && cudaMemsetAsync(B->arena, 0, floats * sizeof(float), h->stream) != cudaSuccess)
+        s = SRJ_ECUDA;
+    if (s != SRJ_OK) {
+        srj_destroy(h);
+        return s;
+    }
+    *out = h;
+    return SRJ_OK;
+}
+
+srj_status srj_solve_batched(srj_handle *h, const double *const *f, double *const *u, double tol,
+                             srj_stats *stats) {
+    if (!h) return SRJ_EINVAL;
+    BatchData *B = h->batch;
+    if (!B) return fail(h, SRJ_EINVAL, "srj_solve_batched: not a batched handle");
+    if (h->opts.selector == SRJ_SEL_MLP && !h->mlp_loaded)
+        return fail(h, SRJ_EINVAL, "srj_solve_batched: learned selector without weights");
+    if (!f || !u || !(tol > 0) || !std::isfinite(tol))
+        return fail(h, SRJ_EINVAL, "srj_solve_batched: null arrays or bad tol");
+    for (int p = 0; p < B->nprob; ++p) {
+        if (!f[p] || !u[p]) return fail(h, SRJ_EINVAL, "srj_solve_batched: null array");
+        B->probs[p].f = f[p];
+        B->probs[p].u = u[p];
+    }
+    CK(cudaMemcpyAsync(B->dprobs, B->probs.data(), B->probs.size() * sizeof(BatchProb),
+                       cudaMemcpyHostToDevice, h->stream));
+    srj_status s = SRJ_OK;
+    if (!B->tuned) {
+        s = batch_autotune(h);
+        if (s != SRJ_OK) return s;
+    }
+    s = batch_build_graph(h, tol);
+    if (s != SRJ_OK) return s;
+    CK(cudaEventRecord(h->ev0, h->stream));
+    s = batch_reset(h);
+    if (s != SRJ_OK) return s;
+    CK(cudaGraphLaunch(B->exec, h->stream));
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaMemcpyAsync(B->hstates, B->dstates, (size_t)B->nprob * sizeof(BatchState),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    srj_status worst = SRJ_OK;
+    for (int p = 0; p < B->nprob; ++p) {
+        const BatchState &S = B->hstates[p];
+        const srj_status ps = status_of(S.result);
+        if (ps != SRJ_OK && worst == SRJ_OK) worst = ps;
+        if (stats) {
+            srj_stats &o = stats[p];
+            std::memset(&o, 0, sizeof(o));
+            o.status = ps;
+            o.final_level = S.final_level;
+            o.sweeps = S.sweeps;
+            o.cycles = S.cycles;
+            o.outer = S.outer;
+            o.passes = S.passes;
+            o.r0 = S.r0;
+            o.rn = S.rn;
+            o.seconds = ms * 1e-3;
+        }
+    }
+    return worst;
+}
+
+srj_status srj_mlp_set_weights(srj_handle *h, const uint16_t *w, int64_t count) {
+    if (!h) return SRJ_EINVAL;
+    if (!w || count != 6617) return fail(h, SRJ_EINVAL, "srj_mlp_set_weights: need 6617 values");
+    CK(cudaMemcpyAsync(h->mlp_w, w, 6617 * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->mlp_loaded = true;
+    return SRJ_OK;
+}
+
 const char *srj_last_error(const srj_handle *h) {
     if (!h) return "srj: invalid handle";
     return h->err.empty() ? "" : h->err.c_str();
@@ -641,6 +1016,15 @@ const char *srj_last_error(const srj_handle *h) {
 
 srj_status srj_destroy(srj_handle *h) {
     if (!h) return SRJ_EINVAL;
+    if (BatchData *B = h->batch) {
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        if (B->graph) cudaGraphDestroy(B->graph);
+        for (void *p : {(void *)B->dprobs, (void *)B->dstates, (void *)B->item_prob,
+                        (void *)B->partials, (void *)B->ndone, (void *)B->arena})
+            dfree(p);
+        if (B->hstates) cudaFreeHost(B->hstates);
+        delete B;
+    }
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -650,7 +1034,7 @@ srj_status srj_destroy(srj_handle *h) {
                     (void *)h->wx32, (void *)h->wy32, (void *)h->wz32, (void *)h->invd32,
                     (void *)h->st, (void *)h->partials, (void *)h->trace_level,
                     (void *)h->trace_rn, (void *)h->sched, (void *)h->opartials,
-                    (void *)h->oticket, (void *)h->onorm2, h->dF, h->dU})
+                    (void *)h->oticket, (void *)h->onorm2, h->dF, h->dU, (void *)h->mlp_w})
         dfree(p);
     if (h->h_st) cudaFreeHost(h->h_st);
     if (h->h_onorm2) cudaFreeHost(h->h_onorm2);

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "mlp.cuh"
 #include "srj_internal.h"
 
 namespace srj {
@@ -26,8 +27,8 @@ struct PassPlan {
     int woff;    // index of this sweep's factor in the tables
 };
 
-__device__ __forceinline__ PassPlan plan_pass(const PassLaunch &a, int depth) {
-    const DevState *st = a.st;
+__device__ __forceinline__ PassPlan plan_pass(const DevState *st, const int *lvl_m,
+                                              const int *lvl_off, int depth) {
     PassPlan p{};
     if (st->status != DST_RUNNING) return p;
     p.run = 1;
@@ -36,19 +37,33 @@ __device__ __forceinline__ PassPlan plan_pass(const PassLaunch &a, int depth) {
         p.resid = 1;
         return p;
     }
-    const int M = a.lvl_m[st->level];
+    const int M = lvl_m[st->level];
     const int rem = M - st->k;
     // A cycle of M sweeps takes floor(M / depth) + 1 passes; the last one does
     // rem < depth sweeps and then the residual of the cycle's final state.
     p.nsw = rem >= depth ? depth : rem;
     p.resid = rem < depth ? 1 : 0;
-    p.woff = a.lvl_off[st->level] + st->k;
+    p.woff = lvl_off[st->level] + st->k;
     return p;
 }
 
-__device__ __forceinline__ int next_level(const DevState *st, const SolveCfg &cfg,
-                                          double ratio, int level) {
+__device__ __forceinline__ PassPlan plan_pass(const PassLaunch &a, int depth) {
+    return plan_pass(a.st, a.lvl_m, a.lvl_off, depth);
+}
+
+__device__ __forceinline__ int next_level(DevState *st, const SolveCfg &cfg, double ratio,
+                                          int level, int mlp_pick) {
     const int top = st->max_level;
+    if (st->selector == DSEL_MLP) {
+        // the network picks; Alg. 1 judges: a picked cycle that did not shrink
+        // the residual hands the next decision back to Alg. 1
+        if (mlp_pick >= 0 && !(st->mlp_last && ratio >= 1.0)) {
+            st->mlp_last = 1;
+            return mlp_pick < top ? mlp_pick : top;
+        }
+        if (st->mlp_last) st->mlp_fallbacks += 1;
+        st->mlp_last = 0;
+    }
     switch (st->selector) {
         case DSEL_INCREASING:
             return level < top ? level + 1 : level;
@@ -63,9 +78,16 @@ __device__ __forceinline__ int next_level(const DevState *st, const SolveCfg &cf
     }
 }
 
-// Executed by one thread of the last CTA of a pass.
+// log of a residual ratio as the selector's features use it
+__device__ __forceinline__ float hist_log(double ratio) {
+    const double l = ratio > 0 ? log(ratio) : -20.0;
+    return (float)(l < -20.0 ? -20.0 : (l > 5.0 ? 5.0 : l));
+}
+
+// Executed by one thread of the last CTA of a pass.  mlp_pick is the learned
+// selector's choice for the next cycle (-1 when not evaluated).
 __device__ void advance_state(DevState *st, const SolveCfg &cfg, const PassPlan &p,
-                              double norm2) {
+                              double norm2, int mlp_pick = -1) {
     st->passes += 1;
     if (p.nsw > 0) {
         st->cur ^= 1;
@@ -87,6 +109,9 @@ __device__ void advance_state(DevState *st, const SolveCfg &cfg, const PassPlan 
     const double ratio = rn / st->rprev;
     st->rprev = rn;
     st->rn = rn;
+    for (int i = 7; i > 0; --i) st->hist[i] = st->hist[i - 1];
+    st->hist[0] = hist_log(ratio);
+    st->nhist = st->nhist < 8 ? st->nhist + 1 : 8;
     const long long c = st->cycles;
     const long long ti = c + st->trace_base;
     if (ti < cfg.trace_cap) {
@@ -106,9 +131,27 @@ __device__ void advance_state(DevState *st, const SolveCfg &cfg, const PassPlan 
     } else if (st->sweeps >= st->max_sweeps) {
         st->status = DST_NOTCONV;
     } else {
-        st->level = next_level(st, cfg, ratio, st->level);
+        st->level = next_level(st, cfg, ratio, st->level, mlp_pick);
         st->k = 0;
     }
+}
+
+// The learned selector's pick for the cycle after the one whose residual this
+// pass completed, evaluated by one full warp (every lane returns it); -1 when
+// the selector is not the network or no cycle ended.
+__device__ __forceinline__ int mlp_pick_at_cycle_end(const DevState *st, const SolveCfg &cfg,
+                                                     const PassPlan &p, double norm2,
+                                                     const int *lvl_m, int lane) {
+    if (!p.resid || st->phase == 0 || st->selector != DSEL_MLP || cfg.mlp_w == nullptr)
+        return -1;
+    const double ratio = sqrt(norm2) / st->rprev;
+    float hist[8];
+    hist[0] = hist_log(ratio);
+    for (int i = 1; i < 8; ++i) hist[i] = st->hist[i - 1];
+    const int nh = st->nhist < 8 ? st->nhist + 1 : 8;
+    float x[kMlpIn];
+    mlp_features(x, hist, nh, st->npoints, st->dim, st->level, lvl_m[st->level]);
+    return mlp_pick_warp(cfg.mlp_w, x, lane, nullptr);
 }
 
 // Deterministic block sum: butterfly within warps, then warps in order.
@@ -150,9 +193,11 @@ __device__ void finish_pass(const PassLaunch &a, const PassPlan &p, double block
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         norm2 = acc;
     }
+    int pick = -1;
+    if (tid < 32) pick = mlp_pick_at_cycle_end(a.st, a.cfg, p, norm2, a.lvl_m, tid);
     if (tid == 0) {
         DevState *st = a.st;
-        advance_state(st, a.cfg, p, norm2);
+        advance_state(st, a.cfg, p, norm2, pick);
         st->ticket = 0;
         __threadfence();
         if (a.cfg.use_cond && st->status != DST_RUNNING)

@@ -71,6 +71,13 @@ struct DevState {
     double r0, rprev, rn;
     unsigned int ticket;  // CTAs finished in the current pass
     unsigned int pad1;
+    // learned selector: history of log ratios (most recent first) and counters
+    float hist[8];
+    int32_t nhist;
+    int32_t mlp_last;       // 1 when the current cycle's level was the network's pick
+    int32_t mlp_fallbacks;  // cycles whose level came from Alg. 1 after a failed pick
+    int32_t dim;
+    double npoints;
 };
 
 // Static per-handle pointers passed by value to the pass kernels.
@@ -81,7 +88,7 @@ struct SolveCfg {
     int32_t trace_cap;
     int32_t use_cond;      // 1 when launched inside a conditional while node
     cudaGraphConditionalHandle cond;
-    const float *mlp_w;    // learned selector weights (nullptr unless loaded)
+    const uint16_t *mlp_w;  // learned selector weights, BF16 (mlp.cuh)
 };
 
 // Grid geometry and constant coefficients.
@@ -148,6 +155,45 @@ Wave2dPlan wave2d_plan(int prec, int T, const GridGeo &g, int num_sms);
 cudaError_t wave2d_prepare(int prec, int T);
 cudaError_t wave2d_launch(const Wave2dPlan &p, const PassLaunch &a, cudaStream_t s);
 cudaError_t add_wave2d_node(const Wave2dPlan &p, const PassLaunch &a, cudaGraph_t body);
+
+// Batched persistent solve of many 2D constant-coefficient problems
+// (kernels_batched.cu).  Per problem: immutable geometry and buffers ...
+struct BatchProb {
+    GridGeo geo;
+    IterBufs inner;   // f = FP32 inner rhs, u[2] / ulo[2] = FP32-pair iterates (padded)
+    const double *f;  // user arrays (dense FP64), set per solve
+    double *u;
+    int nstrips, nsegs, R, nitems, item_base;
+};
+// ... and a state machine OUTER -> INNER -> UPDATE -> OUTER ... -> DONE.
+struct BatchState {
+    DevState in;  // state of the current inner SRJ solve
+    int32_t phase, outer, carry, result, final_level, pad;
+    double r0, rn;  // FP64 outer residual norms
+    long long sweeps, cycles, passes;
+    unsigned int ticket, pad1;
+};
+struct BatchLaunch {
+    const BatchProb *probs;
+    BatchState *states;
+    const int32_t *item_prob;  // problem of every item (problem-major order)
+    double *partials;          // one slot per item
+    unsigned int *ndone;
+    int nprob, total_items;
+    const double *w64;
+    int lvl_m[kNumLevels], lvl_off[kNumLevels];
+    double tol, inner_tol;
+    long long max_sweeps;
+    int max_outer, tol_kind, selector, max_level, fixed_level;
+    int stall_stop;  // 0 while autotuning: inner solves never end, u is untouched
+    SolveCfg cfg;
+};
+int batched_outw(int T);
+int batched_smem(int T);
+int batched_grid(int T, int num_sms);
+cudaError_t batched_prepare(int T);
+cudaError_t batched_launch(int T, int num_sms, const BatchLaunch &b, cudaStream_t s);
+cudaError_t add_batched_node(int T, int num_sms, const BatchLaunch &b, cudaGraph_t body);
 
 // Whole-grid helpers (kernels_generic.cu).
 // FP64 outer residual of the mixed-precision path on dense user arrays:

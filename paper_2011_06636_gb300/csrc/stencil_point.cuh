@@ -98,11 +98,15 @@ struct Point {
     // a = c / D, written as the cheaper sum-then-scale form.
     __device__ __forceinline__ static T t_const(const T *nb, const C *a, C invd, C f, T uc) {
         if constexpr (PREC == PREC_DF) {
-            df32 s = df_mul_f(df_add(nb[0], nb[1]), a[0]);
-            if (DIM > 1) s = df_add(s, df_mul_f(df_add(nb[2], nb[3]), a[1]));
-            if (DIM > 2) s = df_add(s, df_mul_f(df_add(nb[4], nb[5]), a[2]));
-            s = df_add(s, df_two_prod(invd, f));
-            return df_sub(s, uc);
+            if constexpr (DIM == 2) {
+                return df_t2d(nb[0], nb[1], nb[2], nb[3], a[0], a[1], invd, f, uc);
+            } else {
+                df32 s = df_mul_f(df_add(nb[0], nb[1]), a[0]);
+                if (DIM > 1) s = df_add(s, df_mul_f(df_add(nb[2], nb[3]), a[1]));
+                if (DIM > 2) s = df_add(s, df_mul_f(df_add(nb[4], nb[5]), a[2]));
+                s = df_add(s, df_two_prod(invd, f));
+                return df_sub(s, uc);
+            }
         } else {
             T s = a[0] * (nb[0] + nb[1]);
             if (DIM > 1) s += a[1] * (nb[2] + nb[3]);
@@ -112,7 +116,7 @@ struct Point {
     }
 
     __device__ __forceinline__ static T relax(T uc, T t, double omega) {
-        if constexpr (PREC == PREC_DF) return df_add(uc, df_mul_f(t, (float)omega));
+        if constexpr (PREC == PREC_DF) return df_axpy(uc, t, (float)omega);
         else return uc + (C)omega * t;
     }
 

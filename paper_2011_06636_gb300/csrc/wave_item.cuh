@@ -1,0 +1,352 @@
+// wave_item.cuh -- one work item of the temporally blocked 2D SRJ pass: a
+// warp streams a strip of 32*V columns down (or up) a segment of rows, doing
+// up to T relaxed Jacobi sweeps (Sec. 2, Eq. relaxed-jacobi) of the current
+// cycle as a wavefront, and optionally the residual of the final state
+// (Sec. 3, Eq. relative-residual) for the cycle-end norm.
+//
+// Shared by the single-grid pass kernel (kernels_wave2d.cu) and the batched
+// persistent kernel (kernels_batched.cu); everything here is file-local.
+//
+//  * lane l of the warp holds V consecutive columns; horizontal neighbours move
+//    by warp shuffles, so the outer H >= T columns of a strip lose validity one
+//    per sweep and only the inner 32V - 2H columns are written;
+//  * at step t the warp loads row j(t) into level 0 and computes level s at
+//    row j(t) -+ s, keeping the last three rows of every level in registers;
+//  * rows of the iterate and of f arrive through per-warp shared-memory rings
+//    filled by cp.async with zero fill outside the grid (Dirichlet ghosts);
+//    each lane reads back only what it copied, so a per-thread wait suffices.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "stencil_point.cuh"
+#include "srj_internal.h"
+
+namespace srj {
+namespace {
+
+constexpr int kWaveWarps = 8;  // warps per CTA of the wave kernels
+constexpr int kPD = 3;         // prefetch distance (steps)
+
+template <int PREC>
+struct WaveTraits;
+template <>
+struct WaveTraits<PREC_F32> {
+    static constexpr int V = 4;
+    static constexpr int ES = 4;  // bytes per element of the iterate / f
+    static constexpr bool LO = false;
+};
+template <>
+struct WaveTraits<PREC_DF> {
+    static constexpr int V = 4;
+    static constexpr int ES = 4;
+    static constexpr bool LO = true;
+};
+template <>
+struct WaveTraits<PREC_F64> {
+    static constexpr int V = 2;
+    static constexpr int ES = 8;
+    static constexpr bool LO = false;
+};
+
+__host__ __device__ constexpr int wave_halo(int T, int V, int ES) {
+    // multiple of V, and of 16 bytes when the chunks are 16 bytes wide
+    return ES == 8 ? T : ((T + V - 1) / V) * V;
+}
+
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes, bool valid,
+                                         const void *safe) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const void *g = valid ? gmem : safe;
+    const int n = valid ? bytes : 0;
+    if (bytes == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(g), "r"(n));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(g), "r"(n));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <int PREC, int T>
+struct Wave {
+    using Tr = WaveTraits<PREC>;
+    static constexpr int V = Tr::V;
+    static constexpr int WC = 32 * V;                  // strip width (columns)
+    static constexpr int H = wave_halo(T, V, Tr::ES);  // halo columns per side
+    static constexpr int OUTW = WC - 2 * H;            // written columns per strip
+    static constexpr int UR = kPD + 1;                 // iterate ring slots
+    static constexpr int FR = T + 2 + kPD;             // rhs ring slots
+    static constexpr int CHUNK = (Tr::ES == 8 && (H % 2)) ? 8 : 16;
+    static constexpr int ROWB = WC * Tr::ES;           // bytes per ring row
+    static constexpr int SMEM_WARP = (UR * (Tr::LO ? 2 : 1) + FR) * ROWB;
+};
+
+// Everything one item needs: geometry, the source / destination iterates,
+// the right-hand side and this pass's factors.
+template <int PREC, int T>
+struct ItemCtx {
+    using E = typename Elem<PREC>::T;
+    using C = typename Elem<PREC>::C;
+    int nx, ny;
+    long long pitch;
+    const unsigned char *src, *src_lo, *fsrc;
+    E *dst;
+    float *dst_hi, *dst_lo;
+    C omega[T];
+    int nsw;     // sweeps of this pass (levels beyond nsw are identities)
+    int resid;   // 1: accumulate the residual of the final state
+    C diag, invd, acoef[3];
+};
+
+// Process the item (strip, segment [y0, y1)) and return this lane's sum of
+// squared residuals (0 unless c.resid).  The caller owns the warp's ring
+// memory wbase (Wave<PREC,T>::SMEM_WARP bytes).
+template <int PREC, int T>
+__device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip, int y0, int y1,
+                                            int dir, unsigned char *wbase, int lane) {
+    using W = Wave<PREC, T>;
+    using E = typename Elem<PREC>::T;
+    using C = typename Elem<PREC>::C;
+    constexpr int V = W::V;
+    constexpr int ES = WaveTraits<PREC>::ES;
+    constexpr bool LO = WaveTraits<PREC>::LO;
+
+    unsigned char *uring = wbase;
+    unsigned char *uring_lo = wbase + W::UR * W::ROWB;
+    unsigned char *fring = wbase + W::UR * W::ROWB * (LO ? 2 : 1);
+    const long long pitchB = c.pitch * ES;
+
+    const int xs = strip * W::OUTW - W::H;  // first column of the strip
+    const int nsteps = (y1 - y0) + 2 * T + 2;
+    const int jbase = dir > 0 ? y0 - T - 1 : y1 + T;  // j(t) = jbase + dir * t
+    const int col0 = xs + lane * V;                   // this lane's first column
+    const bool edge = (xs < 0) || (xs + W::WC > c.nx);
+    bool colok[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) colok[v] = (col0 + v >= 0) && (col0 + v < c.nx);
+    bool outcol[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int cc = lane * V + v;
+        outcol[v] = (cc >= W::H) && (cc < W::WC - W::H) && colok[v];
+    }
+
+    // issue the copies of step t (row j(t) of the iterate and of f)
+    auto issue = [&](int t) {
+        const int row = jbase + dir * t;
+        const bool rok = (row >= 0) && (row < c.ny);
+        const int us = t % W::UR, fs = t % W::FR;
+#pragma unroll
+        for (int k = 0; k < (V * ES) / W::CHUNK; ++k) {
+            const int colc = col0 + k * (W::CHUNK / ES);
+            const bool ok = rok && colc >= 0 && colc < c.pitch;
+            const long long off = (long long)row * pitchB + (long long)colc * ES;
+            const int so = us * W::ROWB + lane * V * ES + k * W::CHUNK;
+            const int fo = fs * W::ROWB + lane * V * ES + k * W::CHUNK;
+            cp_async(uring + so, c.src + off, W::CHUNK, ok, c.src);
+            if constexpr (LO) cp_async(uring_lo + so, c.src_lo + off, W::CHUNK, ok, c.src_lo);
+            cp_async(fring + fo, c.fsrc + off, W::CHUNK, ok, c.fsrc);
+        }
+    };
+
+    // registers: last three rows of every level 0..T
+    E ring[T + 1][3][V];
+#pragma unroll
+    for (int s = 0; s <= T; ++s)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) ring[s][q][v] = zero_u<PREC>();
+    float kahan_s = 0.f, kahan_c = 0.f;  // FP32 paths: compensated r^2 sum
+    double dsum = 0.0;                   // FP64 path
+
+    __syncwarp();
+    for (int t = 0; t < kPD; ++t) {
+        if (t < nsteps) issue(t);
+        cp_commit();
+    }
+
+    auto load_row = [&](unsigned char *ringb, int slot, int v) -> float {
+        return ((const float *)(ringb + slot * W::ROWB))[lane * V + v];
+    };
+
+    auto step = [&](int t, auto phase_tag) {
+        constexpr int PH = decltype(phase_tag)::value;
+        constexpr int CUR = PH, CEN = (PH + 2) % 3, BEH = (PH + 1) % 3;
+        if (t + kPD < nsteps) issue(t + kPD);
+        cp_commit();
+        cp_wait<kPD>();
+        const int jt = jbase + dir * t;
+        // level 0: row j(t)
+        {
+            const int us = t % W::UR;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if constexpr (PREC == PREC_F64) {
+                    ring[0][CUR][v] = ((const double *)(uring + us * W::ROWB))[lane * V + v];
+                } else if constexpr (LO) {
+                    ring[0][CUR][v] = df32{load_row(uring, us, v), load_row(uring_lo, us, v)};
+                } else {
+                    ring[0][CUR][v] = load_row(uring, us, v);
+                }
+            }
+        }
+        // levels 1..T
+#pragma unroll
+        for (int s = 1; s <= T; ++s) {
+            if (t < 2 * s) continue;  // row not needed by any output
+            const int row = jt - dir * s;
+            if (s > c.nsw) {  // identity level (last pass of a cycle)
+#pragma unroll
+                for (int v = 0; v < V; ++v) ring[s][CUR][v] = ring[s - 1][CEN][v];
+                continue;
+            }
+            const int fs = (t - s) % W::FR;
+            C fv[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if constexpr (PREC == PREC_F64)
+                    fv[v] = ((const double *)(fring + fs * W::ROWB))[lane * V + v];
+                else
+                    fv[v] = load_row(fring, fs, v);
+            }
+            E left, right;
+            if constexpr (LO) {
+                left = df32{__shfl_up_sync(0xffffffffu, ring[s - 1][CEN][V - 1].hi, 1),
+                            __shfl_up_sync(0xffffffffu, ring[s - 1][CEN][V - 1].lo, 1)};
+                right = df32{__shfl_down_sync(0xffffffffu, ring[s - 1][CEN][0].hi, 1),
+                             __shfl_down_sync(0xffffffffu, ring[s - 1][CEN][0].lo, 1)};
+            } else {
+                left = __shfl_up_sync(0xffffffffu, ring[s - 1][CEN][V - 1], 1);
+                right = __shfl_down_sync(0xffffffffu, ring[s - 1][CEN][0], 1);
+            }
+            const bool rok = (row >= 0) && (row < c.ny);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                E nb[6];
+                nb[0] = v > 0 ? ring[s - 1][CEN][v - 1] : left;
+                nb[1] = v < V - 1 ? ring[s - 1][CEN][v + 1] : right;
+                nb[2] = ring[s - 1][BEH][v];
+                nb[3] = ring[s - 1][CUR][v];
+                const E uc = ring[s - 1][CEN][v];
+                const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fv[v], uc);
+                E un = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
+                if (!rok || (edge && !colok[v])) un = zero_u<PREC>();
+                ring[s][CUR][v] = un;
+            }
+        }
+        // output: level T at row j(t) - dir*T
+        {
+            const int row = jt - dir * T;
+            if (c.nsw > 0 && row >= y0 && row < y1) {
+                const long long base = (long long)row * c.pitch + col0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (!outcol[v]) continue;
+                    if constexpr (LO) {
+                        c.dst_hi[base + v] = ring[T][CUR][v].hi;
+                        c.dst_lo[base + v] = ring[T][CUR][v].lo;
+                    } else {
+                        c.dst[base + v] = ring[T][CUR][v];
+                    }
+                }
+            }
+        }
+        // residual of the final state at row j(t) - dir*(T+1)
+        if (c.resid && t >= 2 * T + 2) {
+            const int row = jt - dir * (T + 1);
+            const int fs = (t - T - 1) % W::FR;
+            E left, right;
+            if constexpr (LO) {
+                left = df32{__shfl_up_sync(0xffffffffu, ring[T][CEN][V - 1].hi, 1),
+                            __shfl_up_sync(0xffffffffu, ring[T][CEN][V - 1].lo, 1)};
+                right = df32{__shfl_down_sync(0xffffffffu, ring[T][CEN][0].hi, 1),
+                             __shfl_down_sync(0xffffffffu, ring[T][CEN][0].lo, 1)};
+            } else {
+                left = __shfl_up_sync(0xffffffffu, ring[T][CEN][V - 1], 1);
+                right = __shfl_down_sync(0xffffffffu, ring[T][CEN][0], 1);
+            }
+            if (row >= y0 && row < y1) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (!outcol[v]) continue;
+                    C fvv;
+                    if constexpr (PREC == PREC_F64)
+                        fvv = ((const double *)(fring + fs * W::ROWB))[lane * V + v];
+                    else
+                        fvv = load_row(fring, fs, v);
+                    E nb[6];
+                    nb[0] = v > 0 ? ring[T][CEN][v - 1] : left;
+                    nb[1] = v < V - 1 ? ring[T][CEN][v + 1] : right;
+                    nb[2] = ring[T][BEH][v];
+                    nb[3] = ring[T][CUR][v];
+                    const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fvv, ring[T][CEN][v]);
+                    if constexpr (PREC == PREC_F64) {
+                        const double r = c.diag * tt;
+                        dsum = fma(r, r, dsum);
+                    } else {
+                        float r;
+                        if constexpr (LO) r = c.diag * tt.hi;
+                        else r = c.diag * tt;
+                        // Kahan: sum += r^2
+                        const float y = fmaf(r, r, -kahan_c);
+                        const float sum = kahan_s + y;
+                        kahan_c = (sum - kahan_s) - y;
+                        kahan_s = sum;
+                    }
+                }
+            }
+        }
+    };
+
+    using P0 = std::integral_constant<int, 0>;
+    using P1 = std::integral_constant<int, 1>;
+    using P2 = std::integral_constant<int, 2>;
+    int t = 0;
+    for (; t + 3 <= nsteps; t += 3) {
+        step(t, P0{});
+        step(t + 1, P1{});
+        step(t + 2, P2{});
+    }
+    if (t < nsteps) step(t, P0{});
+    if (t + 1 < nsteps) step(t + 1, P1{});
+    cp_wait<0>();
+    __syncwarp();
+    if constexpr (PREC == PREC_F64) return dsum;
+    else return (double)kahan_s - (double)kahan_c;
+}
+
+// Factors, coefficients and buffers of one pass of one grid.
+template <int PREC, int T>
+__device__ __forceinline__ void fill_ctx(ItemCtx<PREC, T> &c, const GridGeo &g,
+                                         const IterBufs &b, int cur, int nsw, int resid,
+                                         const double *w64, int woff) {
+    using E = typename Elem<PREC>::T;
+    using C = typename Elem<PREC>::C;
+    c.nx = g.nx;
+    c.ny = g.ny;
+    c.pitch = g.pitch;
+    c.src = (const unsigned char *)b.u[cur];
+    c.src_lo = WaveTraits<PREC>::LO ? (const unsigned char *)b.ulo[cur] : nullptr;
+    c.fsrc = (const unsigned char *)b.f;
+    c.dst = (E *)b.u[cur ^ 1];
+    c.dst_hi = (float *)b.u[cur ^ 1];
+    c.dst_lo = (float *)b.ulo[cur ^ 1];
+#pragma unroll
+    for (int s = 0; s < T; ++s) c.omega[s] = (s < nsw) ? (C)w64[woff + s] : C(0);
+    c.nsw = nsw;
+    c.resid = resid;
+    c.diag = C(g.diag);
+    c.invd = C(1.0 / g.diag);
+    c.acoef[0] = C(g.cx / g.diag);
+    c.acoef[1] = C(g.cy / g.diag);
+    c.acoef[2] = C(0);
+}
+
+}  // namespace
+}  // namespace srj

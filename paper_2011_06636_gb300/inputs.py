@@ -23,6 +23,9 @@ Recipes (the paper uses no dataset; every workload is synthetic):
   the others the anisotropic operator -eps u_xx - u_yy with eps log-uniform in
   [1e-2, 1]; f i.i.d. N(0, 1).
 * The paper's own experiments: b = 1 (Sec. 3, Sec. 4.1) and f = 1 (Sec. 4.2.3).
+* Learned selector: initial weights He-uniform (limit sqrt(6 / fan_in)), zero
+  biases, parameter order W1 (64x12), b1, W2 (64x64), b2, W3 (25x64), b3; the
+  minibatch order of training is a seeded permutation per epoch.
 """
 from __future__ import annotations
 
@@ -109,3 +112,25 @@ def batched_problems(count: int = 256, seed: int = 0, smin: int = 64,
         out.append(dict(n=[int(sides[i]), int(sides[i])], eps=[e, 1.0],
                         seed_f=int(seed * 100003 + i)))
     return out
+
+
+MLP_SHAPES = [(64, 12), (64,), (64, 64), (64,), (25, 64), (25,)]
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Initial selector parameters (FP32 vector of 6617 values)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in MLP_SHAPES:
+        if len(s) == 2:
+            lim = math.sqrt(6.0 / s[1])
+            parts.append(rng.uniform(-lim, lim, size=s).ravel())
+        else:
+            parts.append(np.zeros(s))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def minibatch_order(n: int, epochs: int, seed: int) -> np.ndarray:
+    """Sample order for training: one seeded permutation of range(n) per epoch."""
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.permutation(n) for _ in range(epochs)]).astype(np.int32)

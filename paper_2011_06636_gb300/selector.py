@@ -1,0 +1,166 @@
+"""Learned scheme selector: trace collection, training, and the stored weights.
+
+Traces follow the paper's data-collection procedure (Sec. 3): the solver
+starts a problem at level 0; at each later decision it tries the three moves
+(level - 1, same, level + 1) from the same iterate, records the average
+convergence rate -log(r_after / r_before) / M of each (Sec. 3, Eq.
+average-convergence-rate), and continues with one move drawn at random.  Each
+decision becomes one training sample: the features of the state (see
+csrc/mlp.cuh) labelled with the move of the best rate.  Every cycle runs in
+the library (FP64 sweeps through ``srj_run_levels``); training runs in the
+library's CUDA kernel (``srj_mlp_train``).
+
+    python -m paper_2011_06636_gb300.selector --out selector_bf16.bin
+
+writes the BF16 weights (6617 little-endian uint16) next to this file by
+default; ``load_weights()`` reads them back.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS = os.path.join(HERE, "selector_bf16.bin")
+N_PARAMS = 6617
+LEVEL_M = [1, 2, 3, 5, 7, 10, 14, 19, 26, 35, 47, 63, 84, 111, 147, 194, 256, 338, 446, 589,
+           778, 1027, 1356, 1790, 2362]
+
+
+def features(hist, npoints, dim, level):
+    """The 12 selector inputs (same definition as csrc/mlp.cuh)."""
+    x = np.zeros(12, dtype=np.float32)
+    for i, v in enumerate(hist[:8]):
+        x[i] = v
+    x[8] = math.log10(npoints) / 10.0
+    x[9] = dim / 3.0
+    x[10] = level / 24.0
+    x[11] = math.log(LEVEL_M[level]) / math.log(2362.0)
+    return x
+
+
+def _log_ratio(r):
+    return float(min(5.0, max(-20.0, math.log(r)))) if r > 0 else -20.0
+
+
+def collect(problem, seed, max_cycles=120, tol=1e-8):
+    """One trajectory of the paper's data-collection walk on `problem`
+    (dict n, eps, f).  Returns (X, y) lists."""
+    import torch
+
+    from . import srj
+    n = problem["n"]
+    f = torch.as_tensor(np.ascontiguousarray(problem["f"]), device="cuda")
+    h = srj.srj_create(n, eps=problem.get("eps"), precision=srj.SRJ_PREC_F64,
+                       trace_capacity=8)
+    rng = np.random.default_rng(seed)
+    npts = int(np.prod(n))
+    X, y = [], []
+    try:
+        u = torch.zeros_like(f)
+        r0 = srj.srj_residual_norm(h, f.data_ptr(), u.data_ptr())
+        rn = srj.srj_run_levels(h, f.data_ptr(), u.data_ptr(), [0])[0]  # first cycle at level 0
+        hist = [_log_ratio(rn / r0)]
+        level = 0
+        for _ in range(max_cycles):
+            if rn / r0 < tol:
+                break
+            cands = [c for c in (level - 1, level, level + 1) if 0 <= c <= 24]
+            outs = []
+            for c in cands:
+                uc = u.clone()
+                rc = srj.srj_run_levels(h, f.data_ptr(), uc.data_ptr(), [c])[0]
+                rate = -math.log(max(rc, 1e-300) / rn) / LEVEL_M[c]
+                outs.append((rate, c, uc, rc))
+            best = max(outs, key=lambda t: t[0])
+            X.append(features(hist, npts, len(n), level))
+            y.append(best[1])
+            rate, level, u, rnew = outs[int(rng.integers(len(outs)))]
+            hist = [_log_ratio(rnew / rn)] + hist
+            rn = rnew
+    finally:
+        srj.srj_destroy(h)
+    return X, y
+
+
+def training_problems(seed=0):
+    """Seeded 1D and 2D Poisson problems (b = 1 as in Sec. 3 and random f)."""
+    from . import inputs
+    probs = []
+    for N in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096):
+        probs.append({"n": [N], "f": np.ones(N)})
+        probs.append({"n": [N], "f": inputs.uniform_rhs([N], seed=seed + N).ravel()})
+    for s in (16, 32, 64, 128, 256, 512):
+        probs.append({"n": [s, s], "f": np.ones(s * s)})
+        probs.append({"n": [s, s], "f": inputs.uniform_rhs([s, s], seed=seed + s).ravel()})
+    return probs
+
+
+def train(X, y, epochs=40, batch=64, lr=3e-3, seed=0):
+    import torch
+
+    from . import inputs, srj
+    X = np.asarray(X, dtype=np.float32)
+    y = np.asarray(y, dtype=np.int32)
+    n = len(y)
+    order = inputs.minibatch_order(n, epochs, seed)
+    steps = len(order) // batch
+    theta = torch.as_tensor(inputs.mlp_init(seed), device="cuda")
+    xd = torch.as_tensor(X, device="cuda")
+    yd = torch.as_tensor(y, device="cuda")
+    od = torch.as_tensor(order[:steps * batch], device="cuda")
+    loss = srj.srj_mlp_train(xd.data_ptr(), yd.data_ptr(), n, od.data_ptr(), steps, batch, lr,
+                             theta.data_ptr())
+    return theta.cpu().numpy(), loss
+
+
+def to_bf16_bits(theta):
+    a = np.asarray(theta, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return u.astype(np.uint16)
+
+
+def load_weights(path=WEIGHTS):
+    w = np.fromfile(path, dtype="<u2")
+    if w.size != N_PARAMS:
+        raise ValueError("selector weights: expected %d values, got %d" % (N_PARAMS, w.size))
+    return w
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--seeds", type=int, default=3)
+    ap.add_argument("--epochs", type=int, default=40)
+    args = ap.parse_args()
+    t0 = time.time()
+    X, y = [], []
+    for s in range(args.seeds):
+        for i, p in enumerate(training_problems(seed=100 * s)):
+            a, b = collect(p, seed=1000 * s + i)
+            X += a
+            y += b
+    t1 = time.time()
+    theta, loss = train(X, y, epochs=args.epochs)
+    from . import srj
+    bits = to_bf16_bits(theta)
+    picks, _ = srj.srj_mlp_forward(bits, np.asarray(X, dtype=np.float32))
+    acc = float(np.mean(picks == np.asarray(y)))
+    bits.astype("<u2").tofile(args.out)
+    info = {"samples": len(y), "collect_s": t1 - t0, "train_s": time.time() - t1,
+            "loss_first": float(loss[:50].mean()), "loss_last": float(loss[-50:].mean()),
+            "train_accuracy": acc, "epochs": args.epochs,
+            "label_counts": np.bincount(np.asarray(y), minlength=25).tolist()}
+    with open(os.path.splitext(args.out)[0] + ".json", "w") as fh:
+        json.dump(info, fh, indent=1)
+    print(json.dumps(info))
+
+
+if __name__ == "__main__":
+    main()

@@ -24,7 +24,8 @@ SRJ_TOL_REL, SRJ_TOL_ABS = range(2)
 # every entry point include/srj.h declares
 EXPORTS = ["srj_version", "srj_level_m", "srj_scheme_omegas", "srj_create", "srj_solve",
            "srj_solve_host", "srj_run_levels", "srj_residual_norm", "srj_get_trace",
-           "srj_last_error", "srj_destroy"]
+           "srj_create_batched", "srj_solve_batched", "srj_mlp_set_weights", "srj_mlp_forward",
+           "srj_mlp_train", "srj_last_error", "srj_destroy"]
 
 
 class srj_grid(C.Structure):
@@ -89,6 +90,19 @@ def load(build_if_missing: bool = True):
     L.srj_residual_norm.restype = C.c_int
     L.srj_get_trace.argtypes = [H, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_int64]
     L.srj_get_trace.restype = C.c_int64
+    L.srj_create_batched.argtypes = [C.c_int32, C.POINTER(srj_grid), C.POINTER(srj_stencil),
+                                     C.POINTER(srj_opts), C.c_void_p, C.POINTER(H)]
+    L.srj_create_batched.restype = C.c_int
+    L.srj_solve_batched.argtypes = [H, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double,
+                                    C.POINTER(srj_stats)]
+    L.srj_solve_batched.restype = C.c_int
+    L.srj_mlp_set_weights.argtypes = [H, C.c_void_p, C.c_int64]
+    L.srj_mlp_set_weights.restype = C.c_int
+    L.srj_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    L.srj_mlp_forward.restype = C.c_int
+    L.srj_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.srj_mlp_train.restype = C.c_int
     L.srj_last_error.argtypes = [H]
     L.srj_last_error.restype = C.c_char_p
     L.srj_destroy.argtypes = [H]
@@ -200,6 +214,73 @@ def srj_get_trace(h, capacity=100000):
         raise SrjError(SRJ_EINVAL, "srj_get_trace")
     m = min(n, capacity)
     return lv[:m].copy(), rn[:m].copy()
+
+
+def srj_create_batched(ns, eps=None, selector=SRJ_SEL_HEURISTIC, tol_kind=SRJ_TOL_REL,
+                       level0=0, max_level=0, temporal_depth=0, max_sweeps=0, inner_tol=0.0,
+                       stream=None):
+    """ns: list of [nx, ny]; eps: list of [eps_x, eps_y] or None.  Mixed precision."""
+    L = load()
+    n = len(ns)
+    grids = (srj_grid * n)(*[_grid(v) for v in ns])
+    sts = (srj_stencil * n)()
+    for i in range(n):
+        for a in range(2):
+            sts[i].eps[a] = float(eps[i][a]) if eps is not None else 0.0
+        sts[i].k = None
+    o = srj_opts(selector, SRJ_PREC_MIXED, tol_kind, level0, 0, max_level, temporal_depth, 0,
+                 max_sweeps, inner_tol)
+    hnd = C.c_void_p()
+    rc = L.srj_create_batched(n, grids, sts, C.byref(o), stream, C.byref(hnd))
+    if rc != SRJ_OK:
+        raise SrjError(rc, "srj_create_batched")
+    return hnd.value
+
+
+def srj_solve_batched(h, f_ptrs, u_ptrs, tol):
+    """f_ptrs, u_ptrs: lists of device pointers.  Returns (status, [stats dict])."""
+    n = len(f_ptrs)
+    fa = (C.c_void_p * n)(*f_ptrs)
+    ua = (C.c_void_p * n)(*u_ptrs)
+    st = (srj_stats * n)()
+    rc = load().srj_solve_batched(h, fa, ua, float(tol), st)
+    if rc not in (SRJ_OK, SRJ_ENOTCONV, SRJ_EDIVERGED):
+        _check(h, rc, "srj_solve_batched")
+    return rc, [st[i].as_dict() for i in range(n)]
+
+
+def srj_mlp_set_weights(h, w_bits):
+    """w_bits: numpy uint16 array of 6617 BF16 bit patterns."""
+    import numpy as np
+    w = np.ascontiguousarray(w_bits, dtype=np.uint16)
+    rc = load().srj_mlp_set_weights(h, w.ctypes.data, w.size)
+    _check(h, rc, "srj_mlp_set_weights")
+
+
+def srj_mlp_forward(w_bits, X):
+    """Device inference on host features X (n x 12): (picks, logits)."""
+    import numpy as np
+    w = np.ascontiguousarray(w_bits, dtype=np.uint16)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n = X.shape[0]
+    pick = np.zeros(n, dtype=np.int32)
+    logits = np.zeros((n, 25), dtype=np.float32)
+    rc = load().srj_mlp_forward(w.ctypes.data, X.ctypes.data, n, pick.ctypes.data,
+                                logits.ctypes.data)
+    if rc != SRJ_OK:
+        raise SrjError(rc, "srj_mlp_forward")
+    return pick, logits
+
+
+def srj_mlp_train(x_ptr, y_ptr, n, order_ptr, steps, batch, lr, theta_ptr, stream=None):
+    """Device pointers in; returns the per-step minibatch losses (numpy)."""
+    import numpy as np
+    loss = np.zeros(max(int(steps), 1), dtype=np.float32)
+    rc = load().srj_mlp_train(x_ptr, y_ptr, n, order_ptr, steps, batch, lr, theta_ptr,
+                              loss.ctypes.data, stream)
+    if rc != SRJ_OK:
+        raise SrjError(rc, "srj_mlp_train")
+    return loss[:steps]
 
 
 def srj_last_error(h) -> str:
