@@ -231,6 +231,29 @@ srj_status srj_mlp_train(const float *x_dev, const int32_t *y_dev, int64_t n,
                          const int32_t *order_dev, int64_t steps, int32_t batch, float lr,
                          float *theta_dev, float *loss_host, void *stream);
 
+/* FP64 residual norm ||f - A u||_2 (constant coefficients; f, u DEVICE
+ * dense FP64 arrays of the grid; *out on the HOST) computed without
+ * allocating any memory, for callers that cannot call cudaMalloc or cudaFree:
+ * code running under a device-memory pool or budget it does not own, or on a
+ * path where cudaFree's device-wide synchronisation is unacceptable.  The
+ * paper has no counterpart; this is a deployment variant of the residual
+ * reduction that drives Alg. 1.
+ *
+ * Its reduction scratch is a fixed device array inside the library (one
+ * partial sum per grid row plus a counter, about 512 KB, held by every GPU
+ * that loads the library until the process exits), so grids with more than
+ * 65536 rows (n1 * n2 > 65536) are rejected with SRJ_EINVAL; variable
+ * coefficients (stencil->k != NULL) give SRJ_EUNSUPPORTED.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress with
+ * the device current) and caches it; make that first call before any stream
+ * capture.  Every call clears the counter it needs; all calls on a device
+ * share the array, so calls whose work overlaps on the GPU (other streams or
+ * host threads) race and must be serialised by the caller.  Work is queued on
+ * `stream` (NULL = legacy default) and synchronised before returning. */
+srj_status srj_residual_norm_noalloc(const srj_grid *grid, const srj_stencil *stencil,
+                                     const double *f, const double *u, double *out,
+                                     void *stream);
+
 /* Text describing the last failure on h (static storage inside h), or a
  * generic text for h == NULL. */
 const char *srj_last_error(const srj_handle *h);

@@ -25,7 +25,7 @@ SRJ_TOL_REL, SRJ_TOL_ABS = range(2)
 EXPORTS = ["srj_version", "srj_level_m", "srj_scheme_omegas", "srj_create", "srj_solve",
            "srj_solve_host", "srj_run_levels", "srj_residual_norm", "srj_get_trace",
            "srj_create_batched", "srj_solve_batched", "srj_mlp_set_weights", "srj_mlp_forward",
-           "srj_mlp_train", "srj_last_error", "srj_destroy"]
+           "srj_mlp_train", "srj_residual_norm_noalloc", "srj_last_error", "srj_destroy"]
 
 
 class srj_grid(C.Structure):
