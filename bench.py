@@ -244,6 +244,76 @@ def batched_leg(srj, inputs, torch, stream, seed=0, count=256, fp64=True):
     return out
 
 
+# ----------------------------------------------------------- learned selector
+def selector_leg(srj, inputs, torch, stream, seed=0):
+    """Unseen problems for the learned selector: 2D anisotropic (eps_x = 0.01)
+    at 2048^2 and 3D log-normal variable-coefficient diffusion at 256^3, both
+    f ~ N(0,1), rel 1e-8, mixed precision; Alg. 1 vs the network (with Alg. 1
+    as fallback) on the same GPU."""
+    from paper_2011_06636_gb300 import selector
+    if not os.path.exists(selector.WEIGHTS):
+        return {"unavailable": "no trained selector weights (selector_bf16.bin)"}
+    w = selector.load_weights()
+    cases = [("2d_aniso_eps0.01_2048", [2048, 2048], [0.01, 1.0], None),
+             ("3d_lognormal_k_256", [256, 256, 256], None, "k")]
+    out = {}
+    for name, n, eps, kind in cases:
+        f = torch.as_tensor(inputs.normal_rhs(n, seed=seed + 7).ravel(), device="cuda")
+        kt = None
+        if kind:
+            kt = torch.as_tensor(inputs.lognormal_k(n, seed=seed + 8).ravel(), device="cuda")
+        res = {}
+        for label, sel in (("heuristic", srj.SRJ_SEL_HEURISTIC), ("mlp", srj.SRJ_SEL_MLP)):
+            h = srj.srj_create(n, eps=eps, k_ptr=kt.data_ptr() if kt is not None else None,
+                               selector=sel, precision=srj.SRJ_PREC_MIXED,
+                               stream=stream.cuda_stream)
+            if sel == srj.SRJ_SEL_MLP:
+                srj.srj_mlp_set_weights(h, w)
+            u = torch.zeros_like(f)
+            srj.srj_solve(h, f.data_ptr(), u.data_ptr(), TOL)  # warm-up (graph build)
+            u.zero_()
+            st = srj.srj_solve(h, f.data_ptr(), u.data_ptr(), TOL)
+            srj.srj_destroy(h)
+            res[label] = {"time_to_tol_s": st["seconds"], "cycles": st["cycles"],
+                          "sweeps": st["sweeps"], "outer": st["outer"],
+                          "status": srj.STATUS_NAMES[st["status"]]}
+        res["mlp_speedup"] = res["heuristic"]["time_to_tol_s"] / res["mlp"]["time_to_tol_s"]
+        out[name] = res
+    return out
+
+
+def vark3d_leg(srj, inputs, torch, stream, seed=0, side=512, fp64=True):
+    """3D variable-coefficient diffusion -div(k grad u) = f, 7-point stencil,
+    harmonic-mean faces, log k Gaussian random field (correlation 16 cells,
+    sigma 1), f ~ N(0,1), rel 1e-8: mixed precision (FP32-pair inner SRJ
+    inside FP64 refinement) vs plain FP64 SRJ on the same GPU, with the
+    relative difference of the two solutions."""
+    n = [side] * 3
+    f = torch.as_tensor(inputs.normal_rhs(n, seed=seed + 3).ravel(), device="cuda")
+    kt = torch.as_tensor(inputs.lognormal_k(n, seed=seed + 4).ravel(), device="cuda")
+    res = {}
+    sols = {}
+    for label, prec in (("mixed", srj.SRJ_PREC_MIXED), ("plain_fp64", srj.SRJ_PREC_F64)):
+        if label == "plain_fp64" and not fp64:
+            continue
+        h = srj.srj_create(n, k_ptr=kt.data_ptr(), precision=prec, stream=stream.cuda_stream)
+        u = torch.zeros_like(f)
+        st = srj.srj_solve(h, f.data_ptr(), u.data_ptr(), TOL)
+        srj.srj_destroy(h)
+        res[label] = {"time_to_tol_s": st["seconds"], "sweeps": st["sweeps"],
+                      "cycles": st["cycles"], "outer": st["outer"],
+                      "glups": st["sweeps"] * f.numel() / st["seconds"] / 1e9,
+                      "rel_residual": st["rn"] / st["r0"],
+                      "status": srj.STATUS_NAMES[st["status"]]}
+        sols[label] = u
+    if "plain_fp64" in sols:
+        d = torch.linalg.norm(sols["mixed"] - sols["plain_fp64"]) / torch.linalg.norm(
+            sols["plain_fp64"])
+        res["mixed_vs_fp64_rel_solution_diff"] = float(d)
+        res["speedup"] = res["plain_fp64"]["time_to_tol_s"] / res["mixed"]["time_to_tol_s"]
+    return res
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import numpy as np
@@ -352,7 +422,7 @@ def run_ours(args, rank, world):
         f32t = f.float()
         u32 = torch.zeros(npts, dtype=torch.float32, device="cuda")
         h32 = srj.srj_create(n, precision=srj.SRJ_PREC_F32, stream=stream.cuda_stream,
-                             trace_capacity=64)
+                             trace_capacity=64, temporal_depth=args.f32_depth)
         srj.srj_run_levels(h32, f32t.data_ptr(), u32.data_ptr(), levels)  # warm-up
         u32.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -363,11 +433,12 @@ def run_ours(args, rank, world):
         srj.srj_destroy(h32)
         sw32 = sum(srj.srj_level_m(l) for l in levels)
         t32 = e0.elapsed_time(e1) * 1e-3
-        passes32 = sum(srj.srj_level_m(l) // 8 + 1 for l in levels)
+        d32 = args.f32_depth if args.f32_depth else 8
+        passes32 = sum(srj.srj_level_m(l) // d32 + 1 for l in levels)
         pass_s = t32 / passes32
         hbm_peak32, _ = peaks()
         f32 = {"glups": sw32 * npts / t32 / 1e9, "sweeps": sw32, "seconds": t32,
-               "temporal_depth": 8,
+               "temporal_depth": d32,
                "hbm_per_pass_gbs": 12.0 * npts / pass_s / 1e9,
                "hbm_per_pass_frac": 12.0 * npts / pass_s / 1e9 / hbm_peak32,
                "effective_hbm_frac": 12.0 * sw32 * npts / t32 / 1e9 / hbm_peak32,
@@ -377,6 +448,14 @@ def run_ours(args, rank, world):
     batched = None
     if not args.no_batched:
         batched = batched_leg(srj, inputs, torch, stream, seed=rank, fp64=not args.no_fp64)
+
+    sel = None
+    if not args.no_selector:
+        sel = selector_leg(srj, inputs, torch, stream, seed=rank)
+    vark = None
+    if args.with_3d:
+        vark = vark3d_leg(srj, inputs, torch, stream, seed=rank, side=args.side3d,
+                          fp64=not args.no_fp64)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -416,6 +495,8 @@ def run_ours(args, rank, world):
             "plain_fp64": fp64,
             "fp32_sweeps": f32,
             "batched": batched,
+            "learned_selector": sel,
+            "vark3d": vark,
             "mixed_vs_plain_speedup": (fp64["time_to_tol_s"] / (ms_max / args.steps / 1e3))
             if fp64 else None,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
@@ -435,6 +516,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-selector", action="store_true")
+    ap.add_argument("--with-3d", action="store_true", help="add the 3D variable-k leg")
+    ap.add_argument("--side3d", type=int, default=512)
+    ap.add_argument("--f32-depth", type=int, default=0, help="temporal depth of the FP32 leg")
     ap.add_argument("--depth", type=int, default=0, help="temporal depth of the inner pass (0: library)")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs only)")
     args = ap.parse_args()

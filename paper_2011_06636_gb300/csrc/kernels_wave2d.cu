@@ -131,11 +131,12 @@ Wave2dPlan wave2d_plan(int prec, int T, const GridGeo &g, int num_sms) {
     p.smem = c.smem;
     p.block = 32 * kWarps;
     p.nstrips = (g.nx + c.outw - 1) / c.outw;
-    // aim at about one item per resident warp, but keep segments tall enough
-    // that the wavefront warm-up (2T + 2 rows) stays a small fraction of the
-    // work
+    // at most one item per resident warp (an uneven split would leave a few
+    // warps with two items and double the pass time), with segments tall
+    // enough that the wavefront warm-up (about 3T rows) stays small
     const int warps = num_sms * c.per_sm * kWarps;
-    int nsegs = (warps + p.nstrips - 1) / p.nstrips;
+    int nsegs = warps / p.nstrips;
+    if (nsegs < 1) nsegs = 1;
     int R = (g.ny + nsegs - 1) / nsegs;
     const int rmin = 8 * T + 16;
     if (R < rmin) R = rmin;

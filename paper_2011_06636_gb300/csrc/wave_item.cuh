@@ -11,7 +11,12 @@
 //    by warp shuffles, so the outer H >= T columns of a strip lose validity one
 //    per sweep and only the inner 32V - 2H columns are written;
 //  * at step t the warp loads row j(t) into level 0 and computes level s at
-//    row j(t) -+ s, keeping the last three rows of every level in registers;
+//    row j(t) -+ 2s, keeping the last three rows of every level in registers.
+//    With this two-row lag per level, level s at step t reads only rows that
+//    level s-1 produced at steps t-1, t-2, t-3, so the T levels of one step
+//    are independent (T*V independent updates per lane instead of V); levels
+//    run in descending order so that each ring slot is read before it is
+//    overwritten;
 //  * rows of the iterate and of f arrive through per-warp shared-memory rings
 //    filled by cp.async with zero fill outside the grid (Dirichlet ghosts);
 //    each lane reads back only what it copied, so a per-thread wait suffices.
@@ -80,7 +85,7 @@ struct Wave {
     static constexpr int H = wave_halo(T, V, Tr::ES);  // halo columns per side
     static constexpr int OUTW = WC - 2 * H;            // written columns per strip
     static constexpr int UR = kPD + 1;                 // iterate ring slots
-    static constexpr int FR = T + 2 + kPD;             // rhs ring slots
+    static constexpr int FR = 2 * T + 3 + kPD;         // rhs ring slots
     static constexpr int CHUNK = (Tr::ES == 8 && (H % 2)) ? 8 : 16;
     static constexpr int ROWB = WC * Tr::ES;           // bytes per ring row
     static constexpr int SMEM_WARP = (UR * (Tr::LO ? 2 : 1) + FR) * ROWB;
@@ -122,7 +127,10 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
     const long long pitchB = c.pitch * ES;
 
     const int xs = strip * W::OUTW - W::H;  // first column of the strip
-    const int nsteps = (y1 - y0) + 2 * T + 2;
+    // level s at step t holds row j(t) - 2 s dir; the residual at step t is
+    // that of row j(t) - (2T + 2) dir.  Rows loaded: [y0 - T - 1, y1 + T].
+    const int nsteps = (y1 - y0) + 3 * T + 3;
+    const int nload = (y1 - y0) + 2 * T + 2;          // steps that load a row
     const int jbase = dir > 0 ? y0 - T - 1 : y1 + T;  // j(t) = jbase + dir * t
     const int col0 = xs + lane * V;                   // this lane's first column
     const bool edge = (xs < 0) || (xs + W::WC > c.nx);
@@ -139,7 +147,7 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
     // issue the copies of step t (row j(t) of the iterate and of f)
     auto issue = [&](int t) {
         const int row = jbase + dir * t;
-        const bool rok = (row >= 0) && (row < c.ny);
+        const bool rok = (row >= 0) && (row < c.ny) && (t < nload);
         const int us = t % W::UR, fs = t % W::FR;
 #pragma unroll
         for (int k = 0; k < (V * ES) / W::CHUNK; ++k) {
@@ -174,118 +182,52 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
     auto load_row = [&](unsigned char *ringb, int slot, int v) -> float {
         return ((const float *)(ringb + slot * W::ROWB))[lane * V + v];
     };
+    auto load_f = [&](int slot, int v) -> C {
+        if constexpr (PREC == PREC_F64)
+            return ((const double *)(fring + slot * W::ROWB))[lane * V + v];
+        else
+            return load_row(fring, slot, v);
+    };
+    auto shfl_left = [&](const E &x) -> E {
+        if constexpr (LO)
+            return df32{__shfl_up_sync(0xffffffffu, x.hi, 1), __shfl_up_sync(0xffffffffu, x.lo, 1)};
+        else
+            return __shfl_up_sync(0xffffffffu, x, 1);
+    };
+    auto shfl_right = [&](const E &x) -> E {
+        if constexpr (LO)
+            return df32{__shfl_down_sync(0xffffffffu, x.hi, 1),
+                        __shfl_down_sync(0xffffffffu, x.lo, 1)};
+        else
+            return __shfl_down_sync(0xffffffffu, x, 1);
+    };
 
     auto step = [&](int t, auto phase_tag) {
         constexpr int PH = decltype(phase_tag)::value;
-        constexpr int CUR = PH, CEN = (PH + 2) % 3, BEH = (PH + 1) % 3;
+        // ring slots of the rows produced at steps t-1, t-2, t-3 (and t = t-3's)
+        constexpr int S1 = (PH + 2) % 3, S2 = (PH + 1) % 3, S3 = PH;
         if (t + kPD < nsteps) issue(t + kPD);
         cp_commit();
         cp_wait<kPD>();
         const int jt = jbase + dir * t;
-        // level 0: row j(t)
-        {
-            const int us = t % W::UR;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if constexpr (PREC == PREC_F64) {
-                    ring[0][CUR][v] = ((const double *)(uring + us * W::ROWB))[lane * V + v];
-                } else if constexpr (LO) {
-                    ring[0][CUR][v] = df32{load_row(uring, us, v), load_row(uring_lo, us, v)};
-                } else {
-                    ring[0][CUR][v] = load_row(uring, us, v);
-                }
-            }
-        }
-        // levels 1..T
-#pragma unroll
-        for (int s = 1; s <= T; ++s) {
-            if (t < 2 * s) continue;  // row not needed by any output
-            const int row = jt - dir * s;
-            if (s > c.nsw) {  // identity level (last pass of a cycle)
-#pragma unroll
-                for (int v = 0; v < V; ++v) ring[s][CUR][v] = ring[s - 1][CEN][v];
-                continue;
-            }
-            const int fs = (t - s) % W::FR;
-            C fv[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if constexpr (PREC == PREC_F64)
-                    fv[v] = ((const double *)(fring + fs * W::ROWB))[lane * V + v];
-                else
-                    fv[v] = load_row(fring, fs, v);
-            }
-            E left, right;
-            if constexpr (LO) {
-                left = df32{__shfl_up_sync(0xffffffffu, ring[s - 1][CEN][V - 1].hi, 1),
-                            __shfl_up_sync(0xffffffffu, ring[s - 1][CEN][V - 1].lo, 1)};
-                right = df32{__shfl_down_sync(0xffffffffu, ring[s - 1][CEN][0].hi, 1),
-                             __shfl_down_sync(0xffffffffu, ring[s - 1][CEN][0].lo, 1)};
-            } else {
-                left = __shfl_up_sync(0xffffffffu, ring[s - 1][CEN][V - 1], 1);
-                right = __shfl_down_sync(0xffffffffu, ring[s - 1][CEN][0], 1);
-            }
-            const bool rok = (row >= 0) && (row < c.ny);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                E nb[6];
-                nb[0] = v > 0 ? ring[s - 1][CEN][v - 1] : left;
-                nb[1] = v < V - 1 ? ring[s - 1][CEN][v + 1] : right;
-                nb[2] = ring[s - 1][BEH][v];
-                nb[3] = ring[s - 1][CUR][v];
-                const E uc = ring[s - 1][CEN][v];
-                const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fv[v], uc);
-                E un = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
-                if (!rok || (edge && !colok[v])) un = zero_u<PREC>();
-                ring[s][CUR][v] = un;
-            }
-        }
-        // output: level T at row j(t) - dir*T
-        {
-            const int row = jt - dir * T;
-            if (c.nsw > 0 && row >= y0 && row < y1) {
-                const long long base = (long long)row * c.pitch + col0;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if (!outcol[v]) continue;
-                    if constexpr (LO) {
-                        c.dst_hi[base + v] = ring[T][CUR][v].hi;
-                        c.dst_lo[base + v] = ring[T][CUR][v].lo;
-                    } else {
-                        c.dst[base + v] = ring[T][CUR][v];
-                    }
-                }
-            }
-        }
-        // residual of the final state at row j(t) - dir*(T+1)
-        if (c.resid && t >= 2 * T + 2) {
-            const int row = jt - dir * (T + 1);
-            const int fs = (t - T - 1) % W::FR;
-            E left, right;
-            if constexpr (LO) {
-                left = df32{__shfl_up_sync(0xffffffffu, ring[T][CEN][V - 1].hi, 1),
-                            __shfl_up_sync(0xffffffffu, ring[T][CEN][V - 1].lo, 1)};
-                right = df32{__shfl_down_sync(0xffffffffu, ring[T][CEN][0].hi, 1),
-                             __shfl_down_sync(0xffffffffu, ring[T][CEN][0].lo, 1)};
-            } else {
-                left = __shfl_up_sync(0xffffffffu, ring[T][CEN][V - 1], 1);
-                right = __shfl_down_sync(0xffffffffu, ring[T][CEN][0], 1);
-            }
+        // residual of the final state at row j(t) - (2T+2) dir, from level T's
+        // rows of steps t-1, t-2 (centre), t-3 -- before level T overwrites S3
+        if (c.resid && t >= 3 * T + 3) {
+            const int row = jt - dir * (2 * T + 2);
+            const int fs = (t - 2 * T - 2) % W::FR;
+            const E left = shfl_left(ring[T][S2][V - 1]);
+            const E right = shfl_right(ring[T][S2][0]);
             if (row >= y0 && row < y1) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     if (!outcol[v]) continue;
-                    C fvv;
-                    if constexpr (PREC == PREC_F64)
-                        fvv = ((const double *)(fring + fs * W::ROWB))[lane * V + v];
-                    else
-                        fvv = load_row(fring, fs, v);
+                    const C fvv = load_f(fs, v);
                     E nb[6];
-                    nb[0] = v > 0 ? ring[T][CEN][v - 1] : left;
-                    nb[1] = v < V - 1 ? ring[T][CEN][v + 1] : right;
-                    nb[2] = ring[T][BEH][v];
-                    nb[3] = ring[T][CUR][v];
-                    const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fvv, ring[T][CEN][v]);
+                    nb[0] = v > 0 ? ring[T][S2][v - 1] : left;
+                    nb[1] = v < V - 1 ? ring[T][S2][v + 1] : right;
+                    nb[2] = ring[T][S3][v];
+                    nb[3] = ring[T][S1][v];
+                    const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fvv, ring[T][S2][v]);
                     if constexpr (PREC == PREC_F64) {
                         const double r = c.diag * tt;
                         dsum = fma(r, r, dsum);
@@ -299,6 +241,70 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
                         kahan_c = (sum - kahan_s) - y;
                         kahan_s = sum;
                     }
+                }
+            }
+        }
+        // levels T..1 (descending): level s reads level s-1's rows of steps
+        // t-1, t-2, t-3 and writes its row of step t into slot S3
+#pragma unroll
+        for (int s = T; s >= 1; --s) {
+            if (t < 3 * s) continue;                  // above every needed row
+            if (t > nload - 1 + s) continue;          // below every needed row
+            const int row = jt - dir * (2 * s);
+            if (s > c.nsw) {  // identity level (last pass of a cycle)
+#pragma unroll
+                for (int v = 0; v < V; ++v) ring[s][S3][v] = ring[s - 1][S2][v];
+                continue;
+            }
+            const int fs = (t - 2 * s) % W::FR;
+            C fv[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) fv[v] = load_f(fs, v);
+            const E left = shfl_left(ring[s - 1][S2][V - 1]);
+            const E right = shfl_right(ring[s - 1][S2][0]);
+            const bool rok = (row >= 0) && (row < c.ny);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                E nb[6];
+                nb[0] = v > 0 ? ring[s - 1][S2][v - 1] : left;
+                nb[1] = v < V - 1 ? ring[s - 1][S2][v + 1] : right;
+                nb[2] = ring[s - 1][S3][v];
+                nb[3] = ring[s - 1][S1][v];
+                const E uc = ring[s - 1][S2][v];
+                const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fv[v], uc);
+                E un = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
+                if (!rok || (edge && !colok[v])) un = zero_u<PREC>();
+                ring[s][S3][v] = un;
+            }
+        }
+        // output: level T's new row j(t) - 2T dir
+        {
+            const int row = jt - dir * (2 * T);
+            if (c.nsw > 0 && row >= y0 && row < y1) {
+                const long long base = (long long)row * c.pitch + col0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (!outcol[v]) continue;
+                    if constexpr (LO) {
+                        c.dst_hi[base + v] = ring[T][S3][v].hi;
+                        c.dst_lo[base + v] = ring[T][S3][v].lo;
+                    } else {
+                        c.dst[base + v] = ring[T][S3][v];
+                    }
+                }
+            }
+        }
+        // level 0: row j(t), after every level has read slot S3 of level 0
+        {
+            const int us = t % W::UR;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if constexpr (PREC == PREC_F64) {
+                    ring[0][S3][v] = ((const double *)(uring + us * W::ROWB))[lane * V + v];
+                } else if constexpr (LO) {
+                    ring[0][S3][v] = df32{load_row(uring, us, v), load_row(uring_lo, us, v)};
+                } else {
+                    ring[0][S3][v] = load_row(uring, us, v);
                 }
             }
         }

@@ -48,9 +48,11 @@ def _log_ratio(r):
     return float(min(5.0, max(-20.0, math.log(r)))) if r > 0 else -20.0
 
 
-def collect(problem, seed, max_cycles=120, tol=1e-8):
+def collect(problem, seed, max_cycles=120, tol=1e-8, records=None):
     """One trajectory of the paper's data-collection walk on `problem`
-    (dict n, eps, f).  Returns (X, y) lists."""
+    (dict n, eps, f).  Returns (X, y) lists; when `records` is a list, every
+    tried move is appended to it as (previous ratio, level, move, rate), the
+    data of Sec. 3's post-processing."""
     import torch
 
     from . import srj
@@ -78,6 +80,9 @@ def collect(problem, seed, max_cycles=120, tol=1e-8):
                 rate = -math.log(max(rc, 1e-300) / rn) / LEVEL_M[c]
                 outs.append((rate, c, uc, rc))
             best = max(outs, key=lambda t: t[0])
+            if records is not None:
+                for rate_c, c, _, _ in outs:
+                    records.append((math.exp(hist[0]), level, c - level, rate_c))
             X.append(features(hist, npts, len(n), level))
             y.append(best[1])
             rate, level, u, rnew = outs[int(rng.integers(len(outs)))]
@@ -99,6 +104,42 @@ def training_problems(seed=0):
         probs.append({"n": [s, s], "f": np.ones(s * s)})
         probs.append({"n": [s, s], "f": inputs.uniform_rhs([s, s], seed=seed + s).ravel()})
     return probs
+
+
+def analyse(records, n_set=200):
+    """Sec. 3 post-processing of the collected moves: per level, sort by the
+    previous residual ratio, cut into clusters of n_set records, and in each
+    cluster take the mean rate of each move with a 95 % confidence interval;
+    a cluster's winner is the move with the best mean whose interval does not
+    overlap the others'.  Returns the winners (mean ratio, level, move) and
+    the ratio thresholds they imply: the largest ratio won by 'keep' and the
+    smallest ratio won by 'up' (the paper reads 0.2 and 0.4 off this plot)."""
+    rec = np.asarray(records, dtype=np.float64)
+    winners = []
+    for level in np.unique(rec[:, 1]).astype(int):
+        sub = rec[rec[:, 1] == level]
+        sub = sub[np.argsort(sub[:, 0], kind="stable")]
+        for c0 in range(0, len(sub) - n_set + 1, n_set):
+            cl = sub[c0:c0 + n_set]
+            stats = {}
+            for mv in (-1, 0, 1):
+                r = cl[cl[:, 2] == mv][:, 3]
+                if len(r) >= 5:
+                    half = 1.96 * r.std(ddof=1) / math.sqrt(len(r))
+                    stats[mv] = (r.mean(), r.mean() - half, r.mean() + half)
+            if len(stats) < 2:
+                continue
+            best = max(stats, key=lambda m: stats[m][0])
+            if all(stats[best][1] > stats[m][2] for m in stats if m != best):
+                winners.append((float(cl[:, 0].mean()), int(level), int(best)))
+    keep = [w[0] for w in winners if w[2] == 0]
+    up = [w[0] for w in winners if w[2] == 1]
+    down = [w[0] for w in winners if w[2] == -1]
+    return {"clusters_with_winner": len(winners),
+            "keep_max_ratio": max(keep) if keep else None,
+            "down_ratio_range": [min(down), max(down)] if down else None,
+            "up_min_ratio": min(up) if up else None,
+            "winners": winners}
 
 
 def train(X, y, epochs=40, batch=64, lr=3e-3, seed=0):
@@ -140,10 +181,10 @@ def main():
     ap.add_argument("--epochs", type=int, default=40)
     args = ap.parse_args()
     t0 = time.time()
-    X, y = [], []
+    X, y, records = [], [], []
     for s in range(args.seeds):
         for i, p in enumerate(training_problems(seed=100 * s)):
-            a, b = collect(p, seed=1000 * s + i)
+            a, b = collect(p, seed=1000 * s + i, records=records)
             X += a
             y += b
     t1 = time.time()
@@ -156,7 +197,8 @@ def main():
     info = {"samples": len(y), "collect_s": t1 - t0, "train_s": time.time() - t1,
             "loss_first": float(loss[:50].mean()), "loss_last": float(loss[-50:].mean()),
             "train_accuracy": acc, "epochs": args.epochs,
-            "label_counts": np.bincount(np.asarray(y), minlength=25).tolist()}
+            "label_counts": np.bincount(np.asarray(y), minlength=25).tolist(),
+            "sec3_postprocessing": {k: v for k, v in analyse(records).items() if k != "winners"}}
     with open(os.path.splitext(args.out)[0] + ".json", "w") as fh:
         json.dump(info, fh, indent=1)
     print(json.dumps(info))
