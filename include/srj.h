@@ -105,7 +105,9 @@ typedef struct srj_opts {
     int32_t temporal_depth; /* sweeps fused per HBM pass; 0 = library choice */
     int32_t trace_capacity; /* per-cycle records kept (0 means 4096) */
     int64_t max_sweeps;     /* sweep cap per solve (0 means 1000000) */
-    double inner_tol;       /* SRJ_PREC_MIXED: inner relative tolerance (0 means 1e-4) */
+    double inner_tol;       /* SRJ_PREC_MIXED: floor of the inner solves' relative
+                               tolerance; each inner solve aims at the reduction
+                               still needed, but not below this (0 means 1e-6) */
 } srj_opts;
 
 typedef struct srj_stats {

@@ -15,7 +15,8 @@ the library's kernels compute:
   network:       h1 = relu(W1 x + b1)   64 x 12
                  h2 = relu(W2 h1 + b2)  64 x 64
                  z  = W3 h2 + b3        25 x 64   (one logit per level)
-  decision:      argmax z (ties to the lower level)
+  decision:      argmax z over the moves {L-1, L, L+1} from the current
+                 level L inside [0, 24] (ties to the lower level)
   weights:       BF16 (round to nearest even) for inference, FP32 masters for
                  training; parameter vector = W1, b1, W2, b2, W3, b3 row-major.
   training:      softmax cross-entropy, mean over the batch, Adam.
@@ -122,3 +123,10 @@ def adam_step(theta, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1 - beta1 ** t)
     vh = v / (1 - beta2 ** t)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def decide(theta, x, level, top=24):
+    """The selector's next level from features x at current level `level`."""
+    z = forward(theta, np.asarray(x, dtype=np.float64)[None, :])[0]
+    moves = [c for c in (level - 1, level, level + 1) if 0 <= c <= top]
+    return max(moves, key=lambda c: (z[c], -c))

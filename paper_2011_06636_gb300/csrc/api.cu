@@ -337,10 +337,16 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
         }
         CK(cudaMemsetAsync(h->U[0], 0, ebytes, st));
         CK(cudaMemsetAsync(h->Ulo[0], 0, ebytes, st));
+        // the inner solve aims at the reduction still needed (with margin 2),
+        // but not below the FP32-pair accuracy floor opts.inner_tol
+        const double target = h->opts.tol_kind == SRJ_TOL_ABS ? tol : tol * r0;
+        double eta = 0.5 * target / rn;
+        if (eta < h->opts.inner_tol) eta = h->opts.inner_tol;
+        if (eta > 0.5) eta = 0.5;
         const long long inner_cap = max_sweeps - sweeps < kInnerCap ? max_sweeps - sweeps
                                                                     : kInnerCap;
-        init_state(h, *h->h_st, h->opts.inner_tol, SRJ_TOL_REL, h->opts.selector, level,
-                   inner_cap, 1, 0, trace_base);
+        init_state(h, *h->h_st, eta, SRJ_TOL_REL, h->opts.selector, level, inner_cap, 1, 0,
+                   trace_base);
         CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
         s = run_loop(h);
         if (s != SRJ_OK) return s;
@@ -592,7 +598,7 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
     if (o.max_level == 0) o.max_level = kMaxLevel;
     if (o.trace_capacity == 0) o.trace_capacity = 4096;
     if (o.max_sweeps == 0) o.max_sweeps = 1000000LL;
-    if (o.inner_tol == 0) o.inner_tol = 1e-4;
+    if (o.inner_tol == 0) o.inner_tol = 1e-6;
     auto bad = [&](const char *m) {
         delete h;
         (void)m;

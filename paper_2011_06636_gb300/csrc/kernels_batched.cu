@@ -95,8 +95,14 @@ __device__ void finalize_problem(const BatchLaunch &b, int p, const PassPlan &pl
             DevState &in = S.in;
             const int cur = in.cur;  // the cleared buffer
             const long long left = b.max_sweeps - S.sweeps;
+            // aim at the reduction still needed (margin 2), not below the
+            // FP32-pair accuracy floor b.inner_tol
+            const double target = b.tol_kind == SRJ_TOL_ABS ? b.tol : b.tol * S.r0;
+            double eta = 0.5 * target / rn;
+            if (eta < b.inner_tol) eta = b.inner_tol;
+            if (eta > 0.5) eta = 0.5;
             in = DevState{};
-            in.tol = b.inner_tol;
+            in.tol = eta;
             in.tol_kind = SRJ_TOL_REL;
             in.selector = b.selector;
             in.max_level = b.max_level;

@@ -10,7 +10,9 @@
 //           to [-20, 5]), log10(#points)/10, dim/3, level/24,
 //           log(M(level))/log(2362)
 //   h1 = relu(W1 x + b1) (64), h2 = relu(W2 h1 + b2) (64), z = W3 h2 + b3 (25)
-//   pick = argmax z (ties to the lower level)
+//   pick = argmax z over the levels the paper's selector can move to from the
+//          current level L, {L-1, L, L+1} within [0, top] (ties to the lower
+//          level); without a current level (L < 0) over all 25 levels
 // Weights are BF16 (parameter order W1, b1, W2, b2, W3, b3, row-major), every
 // dot product is accumulated in FP32 in index order.
 #pragma once
@@ -42,9 +44,10 @@ __device__ __forceinline__ void mlp_features(float *x, const float *hist, int nh
 }
 
 // Warp-cooperative forward pass; every lane passes the same x and receives
-// the argmax.  logits (optional, lane-indexed) receives z[lane] for lane < 25.
+// the argmax (restricted to the moves from `level` when level >= 0).  logits
+// (optional, lane-indexed) receives z[lane] for lane < 25.
 __device__ __forceinline__ int mlp_pick_warp(const uint16_t *w, const float *x, int lane,
-                                             float *logit_out) {
+                                             float *logit_out, int level = -1, int top = 24) {
     // layer 1: lane owns units lane and lane + 32
     float h1[2];
     for (int q = 0; q < 2; ++q) {
@@ -73,8 +76,10 @@ __device__ __forceinline__ int mlp_pick_warp(const uint16_t *w, const float *x, 
     }
     if (logit_out && lane < kMlpOut) logit_out[lane] = z;
     // argmax, ties to the lower index
-    float best = lane < kMlpOut ? z : -INFINITY;
-    int arg = lane < kMlpOut ? lane : kMlpOut;
+    bool allowed = lane < kMlpOut;
+    if (level >= 0) allowed = allowed && lane >= level - 1 && lane <= level + 1 && lane <= top;
+    float best = allowed ? z : -INFINITY;
+    int arg = allowed ? lane : kMlpOut;
     for (int o = 16; o > 0; o >>= 1) {
         const float ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oa = __shfl_xor_sync(0xffffffffu, arg, o);

@@ -151,7 +151,7 @@ __device__ __forceinline__ int mlp_pick_at_cycle_end(const DevState *st, const S
     const int nh = st->nhist < 8 ? st->nhist + 1 : 8;
     float x[kMlpIn];
     mlp_features(x, hist, nh, st->npoints, st->dim, st->level, lvl_m[st->level]);
-    return mlp_pick_warp(cfg.mlp_w, x, lane, nullptr);
+    return mlp_pick_warp(cfg.mlp_w, x, lane, nullptr, st->level, st->max_level);
 }
 
 // Deterministic block sum: butterfly within warps, then warps in order.

@@ -4,9 +4,13 @@ Traces follow the paper's data-collection procedure (Sec. 3): the solver
 starts a problem at level 0; at each later decision it tries the three moves
 (level - 1, same, level + 1) from the same iterate, records the average
 convergence rate -log(r_after / r_before) / M of each (Sec. 3, Eq.
-average-convergence-rate), and continues with one move drawn at random.  Each
-decision becomes one training sample: the features of the state (see
-csrc/mlp.cuh) labelled with the move of the best rate.  Every cycle runs in
+average-convergence-rate), and continues with one of the moves.  The paper
+draws that move at random; here half of the moves follow the best-rated one
+and half are random, so that trajectories of the larger problems reach the
+high levels they need within a bounded number of cycles (a purely random walk
+spends nearly all its samples at low levels).  Each decision becomes one
+training sample: the features of the state (see csrc/mlp.cuh) labelled with
+the move of the best rate.  Every cycle runs in
 the library (FP64 sweeps through ``srj_run_levels``); training runs in the
 library's CUDA kernel (``srj_mlp_train``).
 
@@ -48,7 +52,7 @@ def _log_ratio(r):
     return float(min(5.0, max(-20.0, math.log(r)))) if r > 0 else -20.0
 
 
-def collect(problem, seed, max_cycles=120, tol=1e-8, records=None):
+def collect(problem, seed, max_cycles=160, tol=1e-8, records=None, greedy=0.5):
     """One trajectory of the paper's data-collection walk on `problem`
     (dict n, eps, f).  Returns (X, y) lists; when `records` is a list, every
     tried move is appended to it as (previous ratio, level, move, rate), the
@@ -85,7 +89,8 @@ def collect(problem, seed, max_cycles=120, tol=1e-8, records=None):
                     records.append((math.exp(hist[0]), level, c - level, rate_c))
             X.append(features(hist, npts, len(n), level))
             y.append(best[1])
-            rate, level, u, rnew = outs[int(rng.integers(len(outs)))]
+            pick = best if rng.random() < greedy else outs[int(rng.integers(len(outs)))]
+            rate, level, u, rnew = pick
             hist = [_log_ratio(rnew / rn)] + hist
             rn = rnew
     finally:
@@ -97,10 +102,10 @@ def training_problems(seed=0):
     """Seeded 1D and 2D Poisson problems (b = 1 as in Sec. 3 and random f)."""
     from . import inputs
     probs = []
-    for N in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096):
+    for N in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384):
         probs.append({"n": [N], "f": np.ones(N)})
         probs.append({"n": [N], "f": inputs.uniform_rhs([N], seed=seed + N).ravel()})
-    for s in (16, 32, 64, 128, 256, 512):
+    for s in (16, 32, 64, 128, 256, 512, 1024):
         probs.append({"n": [s, s], "f": np.ones(s * s)})
         probs.append({"n": [s, s], "f": inputs.uniform_rhs([s, s], seed=seed + s).ravel()})
     return probs

@@ -84,8 +84,9 @@ def test_device_training_matches_oracle_adam(S):
 
 
 def _oracle_mlp_solve(orc, P, f, theta, tol, max_cycles=400):
-    """The solver loop of Sec. 3 with the level chosen by the oracle network,
-    Alg. 1 as fallback after a picked cycle whose residual did not shrink."""
+    """The solver loop of Sec. 3 with the level chosen by the oracle network
+    among the moves {L-1, L, L+1} (ties to the lower level), Alg. 1 as
+    fallback after a picked cycle whose residual did not shrink."""
     u = np.zeros(P.size)
     r0 = orc.residual_norm(P, u, f)
     rprev, level, hist, levels, by_mlp = r0, 0, [], [], False
@@ -105,7 +106,8 @@ def _oracle_mlp_solve(orc, P, f, theta, tol, max_cycles=400):
         else:
             x = M.features([math.exp(v) for v in hist[:8]], npts, len(P.n), level)
             z = M.forward(theta, x[None, :].astype(np.float32).astype(np.float64))[0]
-            level = int(np.argmax(z))
+            moves = [c for c in (level - 1, level, level + 1) if 0 <= c <= 24]
+            level = max(moves, key=lambda c: (z[c], -c))
             by_mlp = True
     raise AssertionError("oracle loop did not converge")
 
