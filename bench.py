@@ -129,24 +129,33 @@ def barrier(world):
         dist.barrier()
 
 
-def allmax(world, v):
+def _reduce(world, v, op):
     if world <= 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allmax(world, v):
+    import torch.distributed as dist
+    return _reduce(world, v, dist.ReduceOp.MAX if world > 1 else None)
 
 
 def allsum(world, v):
-    if world <= 1:
-        return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(world, v, dist.ReduceOp.SUM if world > 1 else None)
+
+
+def replica_throughput(world, lups_local, ms_local):
+    """Whole-job throughput of independent replicas: every rank's grid-point
+    updates over the slowest rank's time.  Returns (GLUP/s, max ms)."""
+    ms_max = allmax(world, ms_local)
+    lups = allsum(world, float(lups_local))
+    return lups / (ms_max * 1e-3) / 1e9, ms_max
 
 
 # ----------------------------------------------------------------- oracle arm
@@ -379,12 +388,10 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
     barrier(world)
     ms = ev0.elapsed_time(ev1)
-    ms_max = allmax(world, ms)
     sweeps = sum(s["sweeps"] for s in stats)
     passes = sum(s["passes"] for s in stats)
     outer = sum(s["outer"] for s in stats)
-    lups = allsum(world, float(sweeps) * npts)
-    value = lups / (ms_max * 1e-3) / 1e9
+    value, ms_max = replica_throughput(world, float(sweeps) * npts, ms)
     ok = all(s["status"] == srj.SRJ_OK for s in stats)
     # relative residual of the last solve, checked independently in FP64 torch
     uu = u.view(side, side)

@@ -69,6 +69,9 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
         T u_zm = (DIM > 2 && z0 > 0) ? load_u<PREC>(a.bufs, src, col + g.plane * (z0 - 1))
                                      : zero_u<PREC>();
         T u_c = (z0 < z1) ? load_u<PREC>(a.bufs, src, col + g.plane * z0) : zero_u<PREC>();
+        // the updates of successive z planes are independent; unrolling lets
+        // their long dependent chains (FP32-pair arithmetic) overlap
+#pragma unroll 4
         for (int z = z0; z < z1; ++z) {
             const long long i = col + g.plane * z;
             T u_zp = (DIM > 2 && z + 1 < g.nz) ? load_u<PREC>(a.bufs, src, i + g.plane)

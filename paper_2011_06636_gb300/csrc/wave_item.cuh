@@ -33,27 +33,33 @@ namespace srj {
 namespace {
 
 constexpr int kWaveWarps = 8;  // warps per CTA of the wave kernels
-constexpr int kPD = 3;         // prefetch distance (steps)
 
+// V: columns per lane; ES: bytes per element; LO: FP32-pair iterate; PD:
+// cp.async prefetch distance in steps.  A step of the FP32 kernel is short
+// (about 40 instructions per level), so it prefetches 6 rows ahead to cover
+// HBM latency; the FP32-pair steps are about 4x longer and need only 3.
 template <int PREC>
 struct WaveTraits;
 template <>
 struct WaveTraits<PREC_F32> {
     static constexpr int V = 4;
-    static constexpr int ES = 4;  // bytes per element of the iterate / f
+    static constexpr int ES = 4;
     static constexpr bool LO = false;
+    static constexpr int PD = 6;
 };
 template <>
 struct WaveTraits<PREC_DF> {
     static constexpr int V = 4;
     static constexpr int ES = 4;
     static constexpr bool LO = true;
+    static constexpr int PD = 3;
 };
 template <>
 struct WaveTraits<PREC_F64> {
     static constexpr int V = 2;
     static constexpr int ES = 8;
     static constexpr bool LO = false;
+    static constexpr int PD = 4;
 };
 
 __host__ __device__ constexpr int wave_halo(int T, int V, int ES) {
@@ -84,8 +90,9 @@ struct Wave {
     static constexpr int WC = 32 * V;                  // strip width (columns)
     static constexpr int H = wave_halo(T, V, Tr::ES);  // halo columns per side
     static constexpr int OUTW = WC - 2 * H;            // written columns per strip
-    static constexpr int UR = kPD + 1;                 // iterate ring slots
-    static constexpr int FR = 2 * T + 3 + kPD;         // rhs ring slots
+    static constexpr int PD = Tr::PD;                  // prefetch distance
+    static constexpr int UR = PD + 1;                  // iterate ring slots
+    static constexpr int FR = 2 * T + 3 + PD;          // rhs ring slots
     static constexpr int CHUNK = (Tr::ES == 8 && (H % 2)) ? 8 : 16;
     static constexpr int ROWB = WC * Tr::ES;           // bytes per ring row
     static constexpr int SMEM_WARP = (UR * (Tr::LO ? 2 : 1) + FR) * ROWB;
@@ -174,7 +181,7 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
     double dsum = 0.0;                   // FP64 path
 
     __syncwarp();
-    for (int t = 0; t < kPD; ++t) {
+    for (int t = 0; t < W::PD; ++t) {
         if (t < nsteps) issue(t);
         cp_commit();
     }
@@ -206,9 +213,9 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
         constexpr int PH = decltype(phase_tag)::value;
         // ring slots of the rows produced at steps t-1, t-2, t-3 (and t = t-3's)
         constexpr int S1 = (PH + 2) % 3, S2 = (PH + 1) % 3, S3 = PH;
-        if (t + kPD < nsteps) issue(t + kPD);
+        if (t + W::PD < nsteps) issue(t + W::PD);
         cp_commit();
-        cp_wait<kPD>();
+        cp_wait<W::PD>();
         const int jt = jbase + dir * t;
         // residual of the final state at row j(t) - (2T+2) dir, from level T's
         // rows of steps t-1, t-2 (centre), t-3 -- before level T overwrites S3

@@ -1,0 +1,45 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks run the replica
+aggregation (sum of every rank's updates over the slowest rank's time), as
+torchrun would launch them on a multi-GPU node."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r "updated" (r + 1) * 1e9 points in (r + 1) * 100 ms
+        value, ms_max = bench.replica_throughput(world, (rank + 1) * 1e9, (rank + 1) * 100.0)
+        bench.barrier(world)
+        out[rank] = (value, ms_max)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_replicas():
+    import torch.multiprocessing as mp
+    world = 2
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        value, ms_max = out[r]
+        assert ms_max == pytest.approx(200.0)
+        # (1e9 + 2e9) updates in 0.2 s = 15 GLUP/s on every rank
+        assert value == pytest.approx(15.0)

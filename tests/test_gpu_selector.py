@@ -114,7 +114,10 @@ def _oracle_mlp_solve(orc, P, f, theta, tol, max_cycles=400):
 
 @pytest.mark.parametrize("n", [[384], [96, 80]])
 def test_selector_solve_matches_oracle_loop(S, orc, n):
-    bits = _bits(21, bias_scale=2.0)
+    """The library's trained weights (committed with the package) drive both
+    the GPU solve and the oracle loop; decisions and solutions must agree."""
+    from paper_2011_06636_gb300 import selector
+    bits = selector.load_weights()
     theta = M.bits_to_f32(bits).astype(np.float64)
     f = inputs.uniform_rhs(n, seed=3).ravel()
     P = orc.Problem(n)
