@@ -60,8 +60,10 @@ __device__ __forceinline__ double df_to_double(df32 a) {
 // 2D constant-coefficient sweep residual in FP32-pair arithmetic:
 //   t = ax (w + e) + ay (s + n) + invd f - u
 // Each pair sum and scaling keeps its rounding error in a low part and the
-// low parts are summed plainly; one renormalisation at the end.  About 45
-// FP32 operations instead of ~70 for the composition of the generic ops.
+// low parts are summed plainly.  The result is left unnormalised (|lo| may
+// exceed half an ulp of hi when hi cancels): df_axpy consumes lo through an
+// FMA and renormalises its own result, and residual norms use hi + lo.
+// 48 FP32 operations.
 __device__ __forceinline__ df32 df_t2d(df32 w, df32 e, df32 s, df32 n, float ax, float ay,
                                        float invd, float f, df32 u) {
     const df32 sx = df_two_sum(w.hi, e.hi);
@@ -79,7 +81,7 @@ __device__ __forceinline__ df32 df_t2d(df32 w, df32 e, df32 s, df32 n, float ax,
     const float lo = __fsub_rn(__fadd_rn(__fadd_rn(__fadd_rn(q.lo, __fadd_rn(pxl, pyl)), b.lo),
                                          __fadd_rn(r1.lo, r2.lo)),
                                u.lo);
-    return df_fast_two_sum(r2.hi, lo);
+    return df32{r2.hi, lo};
 }
 
 // u + omega t with one renormalisation (about 14 FP32 operations).

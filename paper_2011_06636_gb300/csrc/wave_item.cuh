@@ -35,9 +35,8 @@ namespace {
 constexpr int kWaveWarps = 8;  // warps per CTA of the wave kernels
 
 // V: columns per lane; ES: bytes per element; LO: FP32-pair iterate; PD:
-// cp.async prefetch distance in steps.  A step of the FP32 kernel is short
-// (about 40 instructions per level), so it prefetches 6 rows ahead to cover
-// HBM latency; the FP32-pair steps are about 4x longer and need only 3.
+// cp.async prefetch distance in steps (3: measured enough for every
+// precision; 6 did not help the FP32 kernel).
 template <int PREC>
 struct WaveTraits;
 template <>
@@ -45,7 +44,7 @@ struct WaveTraits<PREC_F32> {
     static constexpr int V = 4;
     static constexpr int ES = 4;
     static constexpr bool LO = false;
-    static constexpr int PD = 6;
+    static constexpr int PD = 3;
 };
 template <>
 struct WaveTraits<PREC_DF> {
@@ -59,8 +58,14 @@ struct WaveTraits<PREC_F64> {
     static constexpr int V = 2;
     static constexpr int ES = 8;
     static constexpr bool LO = false;
-    static constexpr int PD = 4;
+    static constexpr int PD = 3;
 };
+
+__host__ __device__ constexpr int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p *= 2;
+    return p;
+}
 
 __host__ __device__ constexpr int wave_halo(int T, int V, int ES) {
     // multiple of V, and of 16 bytes when the chunks are 16 bytes wide
@@ -91,8 +96,10 @@ struct Wave {
     static constexpr int H = wave_halo(T, V, Tr::ES);  // halo columns per side
     static constexpr int OUTW = WC - 2 * H;            // written columns per strip
     static constexpr int PD = Tr::PD;                  // prefetch distance
-    static constexpr int UR = PD + 1;                  // iterate ring slots
-    static constexpr int FR = 2 * T + 3 + PD;          // rhs ring slots
+    // ring slot counts are powers of two so that slot = step & (count - 1)
+    static constexpr int UR = pow2_at_least(PD + 1);          // iterate ring slots
+    static constexpr int FR = pow2_at_least(2 * T + 3 + PD);  // rhs ring slots
+    static constexpr bool VEC_OUT = (H % V) == 0;      // whole lanes are written
     static constexpr int CHUNK = (Tr::ES == 8 && (H % 2)) ? 8 : 16;
     static constexpr int ROWB = WC * Tr::ES;           // bytes per ring row
     static constexpr int SMEM_WARP = (UR * (Tr::LO ? 2 : 1) + FR) * ROWB;
@@ -150,12 +157,15 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
         const int cc = lane * V + v;
         outcol[v] = (cc >= W::H) && (cc < W::WC - W::H) && colok[v];
     }
+    bool whole_lane = true;  // every column of this lane is written
+#pragma unroll
+    for (int v = 0; v < V; ++v) whole_lane = whole_lane && outcol[v];
 
     // issue the copies of step t (row j(t) of the iterate and of f)
     auto issue = [&](int t) {
         const int row = jbase + dir * t;
         const bool rok = (row >= 0) && (row < c.ny) && (t < nload);
-        const int us = t % W::UR, fs = t % W::FR;
+        const int us = t & (W::UR - 1), fs = t & (W::FR - 1);
 #pragma unroll
         for (int k = 0; k < (V * ES) / W::CHUNK; ++k) {
             const int colc = col0 + k * (W::CHUNK / ES);
@@ -186,14 +196,20 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
         cp_commit();
     }
 
-    auto load_row = [&](unsigned char *ringb, int slot, int v) -> float {
-        return ((const float *)(ringb + slot * W::ROWB))[lane * V + v];
-    };
-    auto load_f = [&](int slot, int v) -> C {
-        if constexpr (PREC == PREC_F64)
-            return ((const double *)(fring + slot * W::ROWB))[lane * V + v];
-        else
-            return load_row(fring, slot, v);
+    // one 16-byte shared-memory load of this lane's V values of a ring row
+    auto load_vec = [&](const unsigned char *ringb, int slot, C *out) {
+        const unsigned char *p = ringb + slot * W::ROWB + lane * V * ES;
+        if constexpr (PREC == PREC_F64) {
+            const double2 q = *(const double2 *)p;
+            out[0] = q.x;
+            out[1] = q.y;
+        } else {
+            const float4 q = *(const float4 *)p;
+            out[0] = q.x;
+            out[1] = q.y;
+            out[2] = q.z;
+            out[3] = q.w;
+        }
     };
     auto shfl_left = [&](const E &x) -> E {
         if constexpr (LO)
@@ -221,14 +237,16 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
         // rows of steps t-1, t-2 (centre), t-3 -- before level T overwrites S3
         if (c.resid && t >= 3 * T + 3) {
             const int row = jt - dir * (2 * T + 2);
-            const int fs = (t - 2 * T - 2) % W::FR;
+            const int fs = (t - 2 * T - 2) & (W::FR - 1);
             const E left = shfl_left(ring[T][S2][V - 1]);
             const E right = shfl_right(ring[T][S2][0]);
             if (row >= y0 && row < y1) {
+                C fr[V];
+                load_vec(fring, fs, fr);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     if (!outcol[v]) continue;
-                    const C fvv = load_f(fs, v);
+                    const C fvv = fr[v];
                     E nb[6];
                     nb[0] = v > 0 ? ring[T][S2][v - 1] : left;
                     nb[1] = v < V - 1 ? ring[T][S2][v + 1] : right;
@@ -240,7 +258,7 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
                         dsum = fma(r, r, dsum);
                     } else {
                         float r;
-                        if constexpr (LO) r = c.diag * tt.hi;
+                        if constexpr (LO) r = c.diag * (tt.hi + tt.lo);
                         else r = c.diag * tt;
                         // Kahan: sum += r^2
                         const float y = fmaf(r, r, -kahan_c);
@@ -263,13 +281,11 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
                 for (int v = 0; v < V; ++v) ring[s][S3][v] = ring[s - 1][S2][v];
                 continue;
             }
-            const int fs = (t - 2 * s) % W::FR;
+            const int fs = (t - 2 * s) & (W::FR - 1);
             C fv[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) fv[v] = load_f(fs, v);
+            load_vec(fring, fs, fv);
             const E left = shfl_left(ring[s - 1][S2][V - 1]);
             const E right = shfl_right(ring[s - 1][S2][0]);
-            const bool rok = (row >= 0) && (row < c.ny);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 E nb[6];
@@ -279,9 +295,15 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
                 nb[3] = ring[s - 1][S1][v];
                 const E uc = ring[s - 1][S2][v];
                 const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fv[v], uc);
-                E un = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
-                if (!rok || (edge && !colok[v])) un = zero_u<PREC>();
-                ring[s][S3][v] = un;
+                ring[s][S3][v] = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
+            }
+            // Dirichlet ghosts stay zero (a warp-uniform test: the row is the
+            // same for every lane and `edge` is per strip)
+            if (edge || row < 0 || row >= c.ny) {
+                const bool rok = (row >= 0) && (row < c.ny);
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (!rok || !colok[v]) ring[s][S3][v] = zero_u<PREC>();
             }
         }
         // output: level T's new row j(t) - 2T dir
@@ -289,30 +311,45 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
             const int row = jt - dir * (2 * T);
             if (c.nsw > 0 && row >= y0 && row < y1) {
                 const long long base = (long long)row * c.pitch + col0;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if (!outcol[v]) continue;
+                if (W::VEC_OUT && whole_lane) {  // one 16-byte store per array
                     if constexpr (LO) {
-                        c.dst_hi[base + v] = ring[T][S3][v].hi;
-                        c.dst_lo[base + v] = ring[T][S3][v].lo;
+                        *(float4 *)(c.dst_hi + base) = make_float4(
+                            ring[T][S3][0].hi, ring[T][S3][1].hi, ring[T][S3][2].hi, ring[T][S3][3].hi);
+                        *(float4 *)(c.dst_lo + base) = make_float4(
+                            ring[T][S3][0].lo, ring[T][S3][1].lo, ring[T][S3][2].lo, ring[T][S3][3].lo);
+                    } else if constexpr (PREC == PREC_F64) {
+                        *(double2 *)(c.dst + base) = make_double2(ring[T][S3][0], ring[T][S3][1]);
                     } else {
-                        c.dst[base + v] = ring[T][S3][v];
+                        *(float4 *)(c.dst + base) = make_float4(ring[T][S3][0], ring[T][S3][1],
+                                                                ring[T][S3][2], ring[T][S3][3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        if (!outcol[v]) continue;
+                        if constexpr (LO) {
+                            c.dst_hi[base + v] = ring[T][S3][v].hi;
+                            c.dst_lo[base + v] = ring[T][S3][v].lo;
+                        } else {
+                            c.dst[base + v] = ring[T][S3][v];
+                        }
                     }
                 }
             }
         }
         // level 0: row j(t), after every level has read slot S3 of level 0
         {
-            const int us = t % W::UR;
+            const int us = t & (W::UR - 1);
+            C hi[V];
+            load_vec(uring, us, hi);
+            if constexpr (LO) {
+                C lo[V];
+                load_vec(uring_lo, us, lo);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if constexpr (PREC == PREC_F64) {
-                    ring[0][S3][v] = ((const double *)(uring + us * W::ROWB))[lane * V + v];
-                } else if constexpr (LO) {
-                    ring[0][S3][v] = df32{load_row(uring, us, v), load_row(uring_lo, us, v)};
-                } else {
-                    ring[0][S3][v] = load_row(uring, us, v);
-                }
+                for (int v = 0; v < V; ++v) ring[0][S3][v] = df32{hi[v], lo[v]};
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) ring[0][S3][v] = hi[v];
             }
         }
     };
