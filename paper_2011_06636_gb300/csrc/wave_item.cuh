@@ -125,9 +125,9 @@ struct ItemCtx {
 // Process the item (strip, segment [y0, y1)) and return this lane's sum of
 // squared residuals (0 unless c.resid).  The caller owns the warp's ring
 // memory wbase (Wave<PREC,T>::SMEM_WARP bytes).
-template <int PREC, int T>
-__device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip, int y0, int y1,
-                                            int dir, unsigned char *wbase, int lane) {
+template <int PREC, int T, bool RESID>
+__device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int strip, int y0,
+                                                 int y1, int dir, unsigned char *wbase, int lane) {
     using W = Wave<PREC, T>;
     using E = typename Elem<PREC>::T;
     using C = typename Elem<PREC>::C;
@@ -225,8 +225,11 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
             return __shfl_down_sync(0xffffffffu, x, 1);
     };
 
-    auto step = [&](int t, auto phase_tag) {
+    // CHK: this step may lie in the warm-up or drain range, where some levels
+    // have no needed row; steady steps skip those tests
+    auto step = [&](int t, auto phase_tag, auto chk_tag) {
         constexpr int PH = decltype(phase_tag)::value;
+        constexpr bool CHK = decltype(chk_tag)::value;
         // ring slots of the rows produced at steps t-1, t-2, t-3 (and t = t-3's)
         constexpr int S1 = (PH + 2) % 3, S2 = (PH + 1) % 3, S3 = PH;
         if (t + W::PD < nsteps) issue(t + W::PD);
@@ -235,7 +238,7 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
         const int jt = jbase + dir * t;
         // residual of the final state at row j(t) - (2T+2) dir, from level T's
         // rows of steps t-1, t-2 (centre), t-3 -- before level T overwrites S3
-        if (c.resid && t >= 3 * T + 3) {
+        if (RESID && t >= 3 * T + 3) {
             const int row = jt - dir * (2 * T + 2);
             const int fs = (t - 2 * T - 2) & (W::FR - 1);
             const E left = shfl_left(ring[T][S2][V - 1]);
@@ -273,8 +276,8 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
         // t-1, t-2, t-3 and writes its row of step t into slot S3
 #pragma unroll
         for (int s = T; s >= 1; --s) {
-            if (t < 3 * s) continue;                  // above every needed row
-            if (t > nload - 1 + s) continue;          // below every needed row
+            if (CHK && t < 3 * s) continue;           // above every needed row
+            if (CHK && t > nload - 1 + s) continue;   // below every needed row
             const int row = jt - dir * (2 * s);
             if (s > c.nsw) {  // identity level (last pass of a cycle)
 #pragma unroll
@@ -357,18 +360,44 @@ __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip
     using P0 = std::integral_constant<int, 0>;
     using P1 = std::integral_constant<int, 1>;
     using P2 = std::integral_constant<int, 2>;
+    using Y = std::true_type;
+    using N = std::false_type;
+    // steps [3T, nload] compute every level; the ranges before and after are
+    // run with the per-level tests (boundaries kept on multiples of 3 so the
+    // register-ring phase stays a compile-time constant)
+    const int t_steady = 3 * T;
+    int t_drain = ((nload + 1) / 3) * 3;
+    if (t_drain < t_steady) t_drain = t_steady;
+    if (t_drain > nsteps) t_drain = nsteps;
     int t = 0;
-    for (; t + 3 <= nsteps; t += 3) {
-        step(t, P0{});
-        step(t + 1, P1{});
-        step(t + 2, P2{});
+    for (; t < t_steady && t < nsteps; t += 3) {
+        step(t, P0{}, Y{});
+        if (t + 1 < nsteps) step(t + 1, P1{}, Y{});
+        if (t + 2 < nsteps) step(t + 2, P2{}, Y{});
     }
-    if (t < nsteps) step(t, P0{});
-    if (t + 1 < nsteps) step(t + 1, P1{});
+    for (; t + 3 <= t_drain; t += 3) {
+        step(t, P0{}, N{});
+        step(t + 1, P1{}, N{});
+        step(t + 2, P2{}, N{});
+    }
+    for (; t < nsteps; t += 3) {
+        step(t, P0{}, Y{});
+        if (t + 1 < nsteps) step(t + 1, P1{}, Y{});
+        if (t + 2 < nsteps) step(t + 2, P2{}, Y{});
+    }
     cp_wait<0>();
     __syncwarp();
     if constexpr (PREC == PREC_F64) return dsum;
     else return (double)kahan_s - (double)kahan_c;
+}
+
+// The residual level is compiled only into the variant for the last pass of
+// a cycle.
+template <int PREC, int T>
+__device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip, int y0, int y1,
+                                            int dir, unsigned char *wbase, int lane) {
+    if (c.resid) return wave_item_impl<PREC, T, true>(c, strip, y0, y1, dir, wbase, lane);
+    return wave_item_impl<PREC, T, false>(c, strip, y0, y1, dir, wbase, lane);
 }
 
 // Factors, coefficients and buffers of one pass of one grid.

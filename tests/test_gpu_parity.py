@@ -411,3 +411,23 @@ def test_batched_mixed_against_oracle(S, orc, depth):
         assert rn_true / ref["r0"] < 1e-8, (p, st)
         lam = lam_min_const(p["n"], p["eps"])
         assert np.linalg.norm(ug - ref["u"]) <= (rn_true + ref["rn"]) / lam * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["F64", "F32", "MIXED"])
+@pytest.mark.parametrize("n", [[300], [64, 80], [12, 10, 9]])
+def test_non_finite_input_reports_diverged(S, n, prec):
+    """A NaN planted in f (on the host) makes the first residual norm
+    non-finite; the device-side test stops the solve with SRJ_EDIVERGED."""
+    p = getattr(S, "SRJ_PREC_" + prec)
+    dt = torch.float32 if prec == "F32" else torch.float64
+    size = int(np.prod(n))
+    f = np.ones(size)
+    f[size // 3] = np.nan
+    fd, ud = dev(f, dt), dev(np.zeros(size), dt)
+    h, _ = make(S, n, p)
+    try:
+        st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-8)
+    finally:
+        S.srj_destroy(h)
+    assert st["status"] == S.SRJ_EDIVERGED
+    assert st["sweeps"] == 0
