@@ -77,13 +77,33 @@ enum srj_precision {
 
 enum srj_tol_kind {
     SRJ_TOL_REL = 0,  /* ||f - A u|| / ||f - A u0|| < tol (Sec. 4.2.3, Eq. relative-residual) */
-    SRJ_TOL_ABS = 1   /* ||f - A u|| < tol (Sec. 4.1) */
+    SRJ_TOL_ABS = 1,  /* ||f - A u|| < tol (Sec. 4.1) */
+    SRJ_TOL_DINF = 2  /* ||u^n - u^(n-1)||_inf < tol, the largest change of one sweep
+                         (Sec. 4.2.2, Eq. relative_residual_solution).  Tested after
+                         every sweep, so a solve can end inside a cycle; Alg. 1 still
+                         reads the L2 residual ratio at each cycle end.  SRJ_PREC_F64
+                         and SRJ_PREC_F32 single-problem handles only. */
+};
+
+/* Boundary condition of one grid axis (both ends). */
+enum srj_bc {
+    SRJ_BC_DIRICHLET = 0, /* u = 0 one step outside the n points (Sec. 2, Sec. 4.2.3) */
+    SRJ_BC_NEUMANN = 1    /* du/dn = 0 by a mirrored ghost node (Sec. 4.2.2): the n points
+                             include both boundary nodes (n >= 2) and the node one step
+                             outside takes the value of the node one step inside, so the
+                             central difference of du/dx at the boundary vanishes.
+                             Constant coefficients, SRJ_PREC_F64 / SRJ_PREC_F32
+                             single-problem handles only.  With every axis Neumann, A is
+                             singular (constant vectors span its null space) and A u = f
+                             needs sum(f) = 0, e.g. the paper's Laplace problem f = 0. */
 };
 
 typedef struct srj_grid {
     int32_t dim;   /* 1, 2 or 3 */
-    int64_t n[3];  /* interior points per axis, x first; axes >= dim ignored */
-    double h[3];   /* grid spacing per axis; 0 means 1/(n+1) (unit domain) */
+    int64_t n[3];  /* points per axis, x first; axes >= dim ignored */
+    double h[3];   /* grid spacing per axis; 0 means the unit domain: 1/(n+1) on a
+                      Dirichlet axis, 1/(n-1) on a Neumann axis */
+    int32_t bc[3]; /* enum srj_bc per axis; zero-initialised = Dirichlet everywhere */
 } srj_grid;
 
 typedef struct srj_stencil {
@@ -140,7 +160,9 @@ int32_t srj_scheme_omegas(int32_t level, double *omega_out, int32_t capacity);
  * (stencil may be NULL: Poisson; opts may be NULL: defaults).  stream is a
  * cudaStream_t (NULL = legacy default stream).  Allocates the device
  * workspace (about 3-6 arrays of the grid size) and the scheme tables on the
- * current device.  On failure *out is NULL and the status says why. */
+ * current device.  On failure *out is NULL and the status says why: a Neumann
+ * axis or SRJ_TOL_DINF together with SRJ_PREC_MIXED or variable coefficients
+ * gives SRJ_EUNSUPPORTED, a Neumann axis with fewer than 2 points SRJ_EINVAL. */
 srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil,
                       const srj_opts *opts, void *stream, srj_handle **out);
 
@@ -245,7 +267,7 @@ srj_status srj_mlp_train(const float *x_dev, const int32_t *y_dev, int64_t n,
  * partial sum per grid row plus a counter, about 512 KB, held by every GPU
  * that loads the library until the process exits), so grids with more than
  * 65536 rows (n1 * n2 > 65536) are rejected with SRJ_EINVAL; variable
- * coefficients (stencil->k != NULL) give SRJ_EUNSUPPORTED.  The first call on
+ * coefficients (stencil->k != NULL) and Neumann axes give SRJ_EUNSUPPORTED.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress with
  * the device current) and caches it; make that first call before any stream
  * capture.  Every call clears the counter it needs; all calls on a device

@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
 
 class _Problem(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_long * 3), ("h", C.c_double * 3),
-                ("eps", C.c_double * 3), ("k", C.POINTER(C.c_double))]
+                ("eps", C.c_double * 3), ("k", C.POINTER(C.c_double)), ("bc", C.c_int * 3)]
 
 
 def lib():
@@ -93,19 +93,26 @@ def _f64(a):
 
 
 class Problem:
-    """Structured-grid problem A u = f with zero Dirichlet values.
+    """Structured-grid problem A u = f.
 
-    ``n`` lists interior sizes per axis with x first (x varies fastest in the
-    flattened arrays).  ``h`` defaults to 1/(n+1) per axis (unit domain),
-    ``eps`` to 1 per axis, ``k`` (cell coefficient with one ghost layer, shape
-    reversed from ``n`` i.e. (..., n1+2, n0+2)) to None (constant).
+    ``n`` lists sizes per axis with x first (x varies fastest in the flattened
+    arrays).  ``bc`` per axis: 0 zero Dirichlet (n interior points), 1
+    homogeneous Neumann by a mirrored ghost node (n nodes including both ends,
+    Sec. 4.2.2); default all Dirichlet.  ``h`` defaults to the unit domain,
+    1/(n+1) on a Dirichlet axis and 1/(n-1) on a Neumann axis, ``eps`` to 1 per
+    axis, ``k`` (cell coefficient with one ghost layer, shape reversed from
+    ``n`` i.e. (..., n1+2, n0+2)) to None (constant).
     """
 
-    def __init__(self, n, h=None, eps=None, k=None):
+    def __init__(self, n, h=None, eps=None, k=None, bc=None):
         n = [int(v) for v in n]
         self.dim = len(n)
         self.n = n
-        self.h = [1.0 / (v + 1) for v in n] if h is None else [float(v) for v in h]
+        self.bc = [0] * self.dim if bc is None else [int(v) for v in bc]
+        if h is None:  # unit domain: interior points (Dirichlet) or all nodes (Neumann)
+            self.h = [1.0 / (v - 1) if b == 1 else 1.0 / (v + 1) for v, b in zip(n, self.bc)]
+        else:
+            self.h = [float(v) for v in h]
         self.eps = [1.0] * self.dim if eps is None else [float(v) for v in eps]
         self.k = None if k is None else _f64(k)
         self.size = int(np.prod(n))
@@ -118,6 +125,8 @@ class Problem:
             s.h[a] = self.h[a] if a < self.dim else 1.0
             s.eps[a] = self.eps[a] if a < self.dim else 0.0
         s.k = _dp(self.k) if self.k is not None else C.POINTER(C.c_double)()
+        for a in range(3):
+            s.bc[a] = self.bc[a] if a < self.dim else 0
         self._keep = s
         return C.byref(s)
 
@@ -195,6 +204,7 @@ def next_level(rule: int, ratio: float, level: int) -> int:
 
 
 RULES = {"heuristic": 0, "increasing": 1, "fixed": 2}
+TOL_KINDS = {"rel": 0, "abs": 1, "dinf": 2}
 
 
 def srj_solve(P: Problem, f, u0=None, tol=1e-8, tol_kind="rel",
@@ -208,7 +218,7 @@ def srj_solve(P: Problem, f, u0=None, tol=1e-8, tol_kind="rel",
     tl = np.zeros(trace_cap, dtype=np.int32)
     tr = np.zeros(trace_cap)
     st = lib().oracle_srj_solve(P._c(), _dp(f), _dp(u), float(tol),
-                                0 if tol_kind == "rel" else 1, RULES[rule],
+                                TOL_KINDS[tol_kind], RULES[rule],
                                 int(level0), int(max_sweeps), C.byref(sw),
                                 C.byref(cy), C.byref(r0), C.byref(rn),
                                 tl.ctypes.data_as(C.POINTER(C.c_int)), _dp(tr),
@@ -235,8 +245,7 @@ def jacobi_solve(P: Problem, f, u0=None, tol=1e-8, tol_kind="rel",
     u = np.zeros(P.size) if u0 is None else _f64(u0).ravel().copy()
     sw = C.c_long()
     rn = C.c_double()
-    st = lib().oracle_jacobi_solve(P._c(), _dp(f), _dp(u), float(tol),
-                                   0 if tol_kind == "rel" else 1,
+    st = lib().oracle_jacobi_solve(P._c(), _dp(f), _dp(u), float(tol), TOL_KINDS[tol_kind],
                                    int(check_every), int(max_sweeps),
                                    C.byref(sw), C.byref(rn))
     return dict(u=u, status=st, sweeps=sw.value, rn=rn.value)

@@ -120,8 +120,11 @@ double oracle_amplification(int M, const double *omega, double lambda)
 /* ------------------------------------------------------------------------
  * The linear system A u = f on a structured grid.
  *
- * dim in {1,2,3}; n[a] interior points on axis a (x is axis 0 and varies
- * fastest in memory); zero Dirichlet values outside the interior.
+ * dim in {1,2,3}; n[a] points on axis a (x is axis 0 and varies fastest in
+ * memory).  bc[a] = 0: zero Dirichlet values one step outside the n interior
+ * points; bc[a] = 1: homogeneous Neumann, the n points are all nodes including
+ * both boundary nodes and the ghost node one step outside mirrors the node one
+ * step inside (Sec. 4.2.2, second-order central difference with ghost nodes).
  * Operator (Sec. 3, 1D matrix; Sec. 4.2.2/4.2.3 for 2D/3D, extended with an
  * axis coefficient eps[a] and an optional cell coefficient k):
  *
@@ -138,6 +141,9 @@ typedef struct {
     double h[3];
     double eps[3];
     const double *k; /* NULL or (n0+2)(n1+2)(n2+2) cell values incl. ghosts */
+    int bc[3];       /* per axis: 0 zero Dirichlet, 1 homogeneous Neumann by a
+                        mirrored ghost node (Sec. 4.2.2): u_{-1} = u_1,
+                        u_n = u_{n-2}, the grid points including both ends */
 } oracle_problem;
 
 static long or_npts(const oracle_problem *P)
@@ -170,14 +176,19 @@ static double or_face(const oracle_problem *P, const long p[3], int a, int s)
 }
 
 /* Value of u at the neighbour of interior point p (linear index i) one step
- * s = -1 or +1 along axis a; zero outside the interior (zero Dirichlet). */
+ * s = -1 or +1 along axis a.  Outside the grid: zero for a Dirichlet axis;
+ * for a Neumann axis the ghost node mirrors the node one step inside, so the
+ * central difference of du/dx at the boundary node vanishes (Sec. 4.2.2). */
 static double or_neighbour(const oracle_problem *P, const double *u,
                            const long p[3], long i, int a, int s)
 {
     long stride = 1;
     for (int b = 0; b < a; ++b) stride *= P->n[b];
     const long qa = p[a] + s;
-    if (qa < 0 || qa >= P->n[a]) return 0.0;
+    if (qa < 0 || qa >= P->n[a]) {
+        if (P->bc[a] != 1) return 0.0;
+        return u[i - s * stride]; /* mirror: u_{-1} = u_1, u_n = u_{n-2} */
+    }
     return u[i + s * stride];
 }
 
@@ -277,6 +288,34 @@ void oracle_sweeps(const oracle_problem *P, double *u, const double *f,
     free(tmp);
 }
 
+/* As oracle_sweeps, but after every sweep takes ||x^n - x^{n-1}||_inf
+ * (Sec. 4.2.2, Eq. relative_residual_solution) and stops after the first
+ * sweep where it falls below dtol.  Returns the number of sweeps done. */
+long oracle_sweeps_dinf(const oracle_problem *P, double *u, const double *f,
+                        const double *omega, long count, double dtol, int *reached)
+{
+    const long N = or_npts(P);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)N);
+    long s = 0;
+    *reached = 0;
+    while (s < count) {
+        oracle_sweep(P, u, f, omega[s], tmp);
+        double dmax = 0.0;
+        for (long i = 0; i < N; ++i) {
+            const double d = fabs(tmp[i] - u[i]);
+            if (!(d <= dmax)) dmax = d; /* a NaN change is kept: never below dtol */
+        }
+        memcpy(u, tmp, sizeof(double) * (size_t)N);
+        s += 1;
+        if (dmax < dtol) {
+            *reached = 1;
+            break;
+        }
+    }
+    free(tmp);
+    return s;
+}
+
 /* Sec. 3, Alg. 1 (the data-driven heuristic), with the readings listed at the
  * top of this file.  rule 0 = heuristic, 1 = increasing (Sec. 4, the brute
  * force comparator that raises the level every cycle), 2 = fixed level. */
@@ -293,7 +332,9 @@ int oracle_next_level(int rule, double ratio, int level)
  *   r0 = ||f - A u0||; level = level0; repeat { M sweeps of the level's
  *   scheme; rn = ||f - A u||; ratio = rn / r_prev; stop if converged;
  *   level = Alg. 1(ratio, level) }.
- * tol_kind 0 = relative (Eq. relative-residual), 1 = absolute L2 norm.
+ * tol_kind 0 = relative (Eq. relative-residual), 1 = absolute L2 norm,
+ * 2 = ||x^n - x^{n-1}||_inf < tol after some sweep (Sec. 4.2.2; tested every
+ * sweep, so the solve can stop inside a cycle).
  * Returns 0 converged, 1 sweep cap reached, 2 non-finite residual.
  * Trace arrays (may be NULL) receive per-cycle level, M and rn; at most
  * trace_cap cycles are recorded but the count returned in *cycles_out is the
@@ -311,14 +352,24 @@ int oracle_srj_solve(const oracle_problem *P, const double *f, double *u,
     long sweeps = 0, cycles = 0;
     int status = 1;
     if (r0_out) *r0_out = r0;
-    if (r0 == 0.0 || (tol_kind == 1 && r0 < tol)) {
+    if ((tol_kind != 2 && r0 == 0.0) || (tol_kind == 1 && r0 < tol)) {
         status = 0;
         goto done;
     }
     while (sweeps < max_sweeps) {
         const int M = oracle_level_omegas(level, omega);
-        oracle_sweeps(P, u, f, omega, M);
-        sweeps += M;
+        if (tol_kind == 2) {
+            int reached = 0;
+            sweeps += oracle_sweeps_dinf(P, u, f, omega, M, tol, &reached);
+            if (reached) {
+                rn = oracle_residual_norm(P, u, f);
+                status = 0;
+                break;
+            }
+        } else {
+            oracle_sweeps(P, u, f, omega, M);
+            sweeps += M;
+        }
         rn = oracle_residual_norm(P, u, f);
         if (cycles < trace_cap) {
             if (trace_level) trace_level[cycles] = level;
@@ -331,7 +382,7 @@ int oracle_srj_solve(const oracle_problem *P, const double *f, double *u,
             status = 2;
             break;
         }
-        if ((tol_kind == 0 ? rn / r0 : rn) < tol) {
+        if (tol_kind != 2 && (tol_kind == 0 ? rn / r0 : rn) < tol) {
             status = 0;
             break;
         }
@@ -370,8 +421,15 @@ int oracle_jacobi_solve(const oracle_problem *P, const double *f, double *u,
     long sweeps = 0;
     double rn = r0;
     int status = 1;
-    if (r0 == 0.0) status = 0;
+    if (r0 == 0.0 && tol_kind != 2) status = 0;
     while (status != 0 && sweeps < max_sweeps) {
+        if (tol_kind == 2) {
+            int reached = 0;
+            oracle_sweeps_dinf(P, u, f, &one, 1, tol, &reached);
+            sweeps += 1;
+            if (reached) status = 0;
+            continue;
+        }
         for (long s = 0; s < check_every; ++s) oracle_sweeps(P, u, f, &one, 1);
         sweeps += check_every;
         rn = oracle_residual_norm(P, u, f);

@@ -140,6 +140,7 @@ PassLaunch make_launch(srj_handle *h, bool inner) {
         a.bufs.invd = f64 ? (const void *)h->invd64 : (const void *)h->invd32;
     }
     (void)inner;
+    a.dinf = h->opts.tol_kind == SRJ_TOL_DINF;
     a.st = h->st;
     a.partials = h->partials;
     a.partials_cap = h->partials_cap;
@@ -267,7 +268,21 @@ srj_status solve_plain(srj_handle *h, const void *f, void *u, double tol, int se
         stats->r0 = r.r0;
         stats->rn = r.rn;
     }
-    return status_of(r.status);
+    const srj_status result = status_of(r.status);
+    if (h->opts.tol_kind == SRJ_TOL_DINF && stats) {
+        // the per-sweep test can end a solve inside a cycle, after the last
+        // cycle-end residual: take ||f - A u|| of the final iterate
+        const DevState fin = r;
+        init_state(h, *h->h_st, 1.0, SRJ_TOL_REL, DSEL_HEURISTIC, 0, 0, 0, 0, 0);
+        h->h_st->cur = fin.cur;
+        CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
+        PassLaunch a = make_launch(h, false);
+        CK(generic_pass_launch(h->kprec, h->vark, a, st));
+        CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        stats->rn = h->h_st->r0;
+    }
+    return result;
 }
 
 // FP64 iterative refinement around FP32-arithmetic inner SRJ solves.
@@ -587,10 +602,23 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
     if (out) *out = nullptr;
     if (!grid || !out) return SRJ_EINVAL;
     if (grid->dim < 1 || grid->dim > 3) return SRJ_EINVAL;
-    for (int a = 0; a < grid->dim; ++a)
+    int neu = 0;
+    for (int a = 0; a < grid->dim; ++a) {
         if (grid->n[a] < 1 || grid->n[a] > (1LL << 30) || grid->h[a] < 0 ||
             !std::isfinite(grid->h[a]))
             return SRJ_EINVAL;
+        if (grid->bc[a] != SRJ_BC_DIRICHLET && grid->bc[a] != SRJ_BC_NEUMANN) return SRJ_EINVAL;
+        if (grid->bc[a] == SRJ_BC_NEUMANN) {
+            if (grid->n[a] < 2) return SRJ_EINVAL;
+            neu |= 1 << a;
+        }
+    }
+    if (neu || (opts && opts->tol_kind == SRJ_TOL_DINF)) {
+        // mirrored ghosts and the per-sweep change test live in the one-sweep
+        // pass kernel, for constant coefficients and one-level arithmetic
+        if ((stencil && stencil->k) || (opts && opts->precision == SRJ_PREC_MIXED))
+            return SRJ_EUNSUPPORTED;
+    }
     h = new (std::nothrow) srj_handle();
     if (!h) return SRJ_ENOMEM;
     srj_opts o{};
@@ -606,7 +634,8 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
     };
     if (o.selector < 0 || o.selector > SRJ_SEL_MLP) return bad("selector");
     if (o.precision < 0 || o.precision > SRJ_PREC_MIXED) return bad("precision");
-    if (o.tol_kind != SRJ_TOL_REL && o.tol_kind != SRJ_TOL_ABS) return bad("tol_kind");
+    if (o.tol_kind != SRJ_TOL_REL && o.tol_kind != SRJ_TOL_ABS && o.tol_kind != SRJ_TOL_DINF)
+        return bad("tol_kind");
     if (o.max_level < 0 || o.max_level > kMaxLevel) return bad("max_level");
     if (o.level0 < 0 || o.level0 > o.max_level) return bad("level0");
     if (o.fixed_level < 0 || o.fixed_level > o.max_level) return bad("fixed_level");
@@ -627,7 +656,11 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
     double hh[3], ee[3];
     for (int a = 0; a < 3; ++a) {
         const long long na = a == 0 ? g.nx : (a == 1 ? g.ny : g.nz);
-        hh[a] = (a < grid->dim && grid->h[a] > 0) ? grid->h[a] : 1.0 / (double)(na + 1);
+        // unit domain: n interior points (Dirichlet) or n nodes incl. both ends (Neumann)
+        const bool na_neu = (neu >> a) & 1;
+        hh[a] = (a < grid->dim && grid->h[a] > 0)
+                    ? grid->h[a]
+                    : 1.0 / (double)(na_neu ? na - 1 : na + 1);
         const double e = stencil ? stencil->eps[a] : 0.0;
         if (e < 0 || !std::isfinite(e)) return bad("eps");
         ee[a] = e > 0 ? e : 1.0;
@@ -636,6 +669,7 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
     g.cy = g.dim > 1 ? ee[1] / (hh[1] * hh[1]) : 0.0;
     g.cz = g.dim > 2 ? ee[2] / (hh[2] * hh[2]) : 0.0;
     g.diag = 2.0 * (g.cx + g.cy + g.cz);
+    g.neu = neu;
     g.pitch = ((long long)g.nx + 31) / 32 * 32;
     g.plane = g.pitch * g.ny;
     h->npts = (long long)g.nx * g.ny * g.nz;
@@ -684,7 +718,7 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
             h->num_sms <= 0)
             h->num_sms = 152;
     }
-    h->use_wave = (g.dim == 2) && !h->vark;
+    h->use_wave = (g.dim == 2) && !h->vark && !neu && o.tol_kind != SRJ_TOL_DINF;
     {
         const char *lm = std::getenv("SRJ_LAUNCH");
         h->host_loop = lm && std::strcmp(lm, "host") == 0;
@@ -875,7 +909,8 @@ srj_status srj_create_batched(int32_t nprob, const srj_grid *grids, const srj_st
     if (o.temporal_depth != 0 && o.temporal_depth != 2 && o.temporal_depth != 4)
         return SRJ_EINVAL;
     for (int p = 0; p < nprob; ++p) {
-        if (grids[p].dim != 2 || (stencils && stencils[p].k)) return SRJ_EUNSUPPORTED;
+        if (grids[p].dim != 2 || (stencils && stencils[p].k) || grids[p].bc[0] || grids[p].bc[1])
+            return SRJ_EUNSUPPORTED;
         if (grids[p].n[0] < 1 || grids[p].n[1] < 1 || grids[p].n[0] > (1 << 20) ||
             grids[p].n[1] > (1 << 20))
             return SRJ_EINVAL;

@@ -64,6 +64,10 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
     cconst[2] = C(g.cz / g.diag);
 
     double part = 0.0;
+    // Neumann axes (Sec. 4.2.2): the ghost node one step outside mirrors the
+    // node one step inside; Dirichlet axes read zero there
+    const bool nx_ = g.neu & 1, ny_ = g.neu & 2, nz_ = g.neu & 4;
+    const bool dinf = a.dinf && p.nsw;
     if (active) {
         const long long col = (long long)x + g.pitch * y;
         T u_zm = (DIM > 2 && z0 > 0) ? load_u<PREC>(a.bufs, src, col + g.plane * (z0 - 1))
@@ -77,14 +81,19 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
             T u_zp = (DIM > 2 && z + 1 < g.nz) ? load_u<PREC>(a.bufs, src, i + g.plane)
                                                : zero_u<PREC>();
             T nb[6];
-            nb[0] = x > 0 ? load_u<PREC>(a.bufs, src, i - 1) : zero_u<PREC>();
-            nb[1] = x + 1 < g.nx ? load_u<PREC>(a.bufs, src, i + 1) : zero_u<PREC>();
+            nb[0] = x > 0 ? load_u<PREC>(a.bufs, src, i - 1)
+                          : (nx_ ? load_u<PREC>(a.bufs, src, i + 1) : zero_u<PREC>());
+            nb[1] = x + 1 < g.nx ? load_u<PREC>(a.bufs, src, i + 1)
+                                 : (nx_ ? load_u<PREC>(a.bufs, src, i - 1) : zero_u<PREC>());
             if (DIM > 1) {
-                nb[2] = y > 0 ? load_u<PREC>(a.bufs, src, i - g.pitch) : zero_u<PREC>();
-                nb[3] = y + 1 < g.ny ? load_u<PREC>(a.bufs, src, i + g.pitch) : zero_u<PREC>();
+                nb[2] = y > 0 ? load_u<PREC>(a.bufs, src, i - g.pitch)
+                              : (ny_ ? load_u<PREC>(a.bufs, src, i + g.pitch) : zero_u<PREC>());
+                nb[3] = y + 1 < g.ny
+                            ? load_u<PREC>(a.bufs, src, i + g.pitch)
+                            : (ny_ ? load_u<PREC>(a.bufs, src, i - g.pitch) : zero_u<PREC>());
             }
-            nb[4] = u_zm;
-            nb[5] = u_zp;
+            nb[4] = (DIM > 2 && nz_ && z == 0) ? u_zp : u_zm;
+            nb[5] = (DIM > 2 && nz_ && z + 1 == g.nz) ? u_zm : u_zp;
             const C fi = f[i];
             T t;
             C diag_i = diag_c;
@@ -109,15 +118,22 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
             } else {
                 t = P::t_const(nb, cconst, invd_c, fi, u_c);
             }
-            if (p.nsw) store_u<PREC>(a.bufs, dst, i, P::relax(u_c, t, omega));
-            else part += P::resid2(t, diag_i);
+            if (p.nsw) {
+                const T un = P::relax(u_c, t, omega);
+                store_u<PREC>(a.bufs, dst, i, un);
+                if constexpr (PREC != PREC_DF)
+                    if (dinf) part = nan_max(part, fabs((double)un - (double)u_c));
+            } else {
+                part += P::resid2(t, diag_i);
+            }
             u_zm = u_c;
             u_c = u_zp;
         }
     }
     double tot = 0.0;
     if (p.resid) tot = block_sum(part);
-    finish_pass(a, p, tot);
+    else if (dinf) tot = block_max(part);
+    finish_pass(a, p, tot, dinf);
 }
 
 template <int PREC, int DIM, bool VARK>

@@ -98,6 +98,8 @@ extern "C" srj_status srj_residual_norm_noalloc(const srj_grid *grid, const srj_
     if (!grid || !f || !u || !out) return SRJ_EINVAL;
     if (grid->dim < 1 || grid->dim > 3) return SRJ_EINVAL;
     if (stencil && stencil->k) return SRJ_EUNSUPPORTED;
+    for (int a = 0; a < grid->dim; ++a)
+        if (grid->bc[a] != SRJ_BC_DIRICHLET) return SRJ_EUNSUPPORTED;
     long long n[3] = {1, 1, 1};
     double c[3] = {0, 0, 0};
     for (int a = 0; a < grid->dim; ++a) {

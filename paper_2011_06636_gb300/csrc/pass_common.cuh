@@ -85,14 +85,24 @@ __device__ __forceinline__ float hist_log(double ratio) {
 }
 
 // Executed by one thread of the last CTA of a pass.  mlp_pick is the learned
-// selector's choice for the next cycle (-1 when not evaluated).
+// selector's choice for the next cycle (-1 when not evaluated); dmax is the
+// largest |u' - u| of this pass's sweep (negative when not measured).
 __device__ void advance_state(DevState *st, const SolveCfg &cfg, const PassPlan &p,
-                              double norm2, int mlp_pick = -1) {
+                              double norm2, int mlp_pick = -1, double dmax = -1.0) {
     st->passes += 1;
     if (p.nsw > 0) {
         st->cur ^= 1;
         st->k += p.nsw;
         st->sweeps += p.nsw;
+        if (dmax >= 0.0 || dmax != dmax) {
+            // Sec. 4.2.2: stop after the first sweep whose largest change is
+            // below tol, inside the cycle if need be (NaN never is)
+            st->dlast = dmax;
+            if (dmax < st->tol) {
+                st->status = DST_CONVERGED;
+                return;
+            }
+        }
     }
     if (!p.resid) return;
     const double rn = sqrt(norm2);
@@ -102,7 +112,8 @@ __device__ void advance_state(DevState *st, const SolveCfg &cfg, const PassPlan 
         st->rprev = rn;
         st->rn = rn;
         if (!isfinite(rn)) st->status = DST_DIVERGED;
-        else if (rn == 0.0 || (st->tol_kind == SRJ_TOL_ABS && rn < st->tol))
+        else if (st->tol_kind != SRJ_TOL_DINF &&
+                 (rn == 0.0 || (st->tol_kind == SRJ_TOL_ABS && rn < st->tol)))
             st->status = DST_CONVERGED;
         return;
     }
@@ -122,7 +133,7 @@ __device__ void advance_state(DevState *st, const SolveCfg &cfg, const PassPlan 
     const double test = (st->tol_kind == SRJ_TOL_ABS) ? rn : rn / st->r0;
     if (!isfinite(rn)) {
         st->status = DST_DIVERGED;
-    } else if (test < st->tol) {
+    } else if (st->tol_kind != SRJ_TOL_DINF && test < st->tol) {
         st->status = DST_CONVERGED;
     } else if (st->selector == DSEL_SCHEDULE && st->cycles >= st->nsched) {
         st->status = DST_DONE;
@@ -168,15 +179,38 @@ __device__ __forceinline__ double block_sum(double v) {
     return t;  // valid in thread 0
 }
 
+// max that keeps a NaN (fmax would drop it)
+__device__ __forceinline__ double nan_max(double a, double b) {
+    return (b > a || b != b) ? b : a;
+}
+
+// Block max with NaN kept (order-independent, so deterministic).
+__device__ __forceinline__ double block_max(double v) {
+    __shared__ double s_warp[32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nthreads = blockDim.x * blockDim.y;
+    for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((tid & 31) == 0) s_warp[tid >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < (nthreads + 31) / 32; ++w) t = nan_max(t, s_warp[w]);
+    return t;  // valid in thread 0
+}
+
 // Ticket + last-CTA finish, shared by all pass kernels.  block_total is the
-// CTA's partial (valid in thread 0).  Returns after the bookkeeping.
-__device__ void finish_pass(const PassLaunch &a, const PassPlan &p, double block_total) {
+// CTA's partial (valid in thread 0): the residual sum of a residual pass, or,
+// with dinf set, the largest |u' - u| of a sweep pass.  Returns after the
+// bookkeeping.
+__device__ void finish_pass(const PassLaunch &a, const PassPlan &p, double block_total,
+                            bool dinf = false) {
     __shared__ int s_last;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const bool dpass = dinf && p.nsw > 0;
     if (tid == 0) {
-        if (p.resid) a.partials[bid] = block_total;
+        if (p.resid || dpass) a.partials[bid] = block_total;
         __threadfence();
         const unsigned int t = atomicAdd(&a.st->ticket, 1u);
         s_last = (t == nblocks - 1);
@@ -184,7 +218,7 @@ __device__ void finish_pass(const PassLaunch &a, const PassPlan &p, double block
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double norm2 = 0.0;
+    double norm2 = 0.0, dmax = -1.0;
     if (p.resid && tid < 32) {
         // fixed assignment of partials to lanes, fixed butterfly: deterministic
         double acc = 0.0;
@@ -193,11 +227,18 @@ __device__ void finish_pass(const PassLaunch &a, const PassPlan &p, double block
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         norm2 = acc;
     }
+    if (dpass && tid < 32) {
+        double acc = 0.0;
+        const volatile double *part = a.partials;
+        for (unsigned int i = tid; i < nblocks; i += 32) acc = nan_max(acc, part[i]);
+        for (int o = 16; o > 0; o >>= 1) acc = nan_max(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        dmax = acc;
+    }
     int pick = -1;
     if (tid < 32) pick = mlp_pick_at_cycle_end(a.st, a.cfg, p, norm2, a.lvl_m, tid);
     if (tid == 0) {
         DevState *st = a.st;
-        advance_state(st, a.cfg, p, norm2, pick);
+        advance_state(st, a.cfg, p, norm2, pick, dmax);
         st->ticket = 0;
         __threadfence();
         if (a.cfg.use_cond && st->status != DST_RUNNING)

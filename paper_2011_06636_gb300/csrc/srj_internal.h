@@ -78,6 +78,7 @@ struct DevState {
     int32_t mlp_fallbacks;  // cycles whose level came from Alg. 1 after a failed pick
     int32_t dim;
     double npoints;
+    double dlast;  // SRJ_TOL_DINF: ||u^n - u^(n-1)||_inf of the latest sweep
 };
 
 // Static per-handle pointers passed by value to the pass kernels.
@@ -98,6 +99,8 @@ struct GridGeo {
     long long pitch, plane;
     double cx, cy, cz;  // eps_a / h_a^2
     double diag;        // 2 (cx + cy + cz) for constant coefficients
+    int32_t neu;        // bit a set: axis a has mirrored-ghost Neumann ends (Sec. 4.2.2)
+    int32_t pad;
 };
 
 enum Prec : int32_t { PREC_F64 = 0, PREC_F32 = 1, PREC_DF = 2 };
@@ -126,6 +129,7 @@ struct PassLaunch {
     SolveCfg cfg;
     int lvl_m[kNumLevels];    // App. B: M of each level
     int lvl_off[kNumLevels];  // offset of each level's factors in w64 / w32
+    int dinf;                 // 1: sweep passes also reduce max |u' - u| (SRJ_TOL_DINF)
 };
 
 // Launch helpers implemented in kernels_generic.cu.  Each returns the CUDA

@@ -19,7 +19,8 @@ STATUS_NAMES = ["SRJ_OK", "SRJ_EINVAL", "SRJ_ENOMEM", "SRJ_ECUDA", "SRJ_ENOTCONV
                 "SRJ_EDIVERGED", "SRJ_ETIMEOUT", "SRJ_EUNSUPPORTED"]
 SRJ_SEL_HEURISTIC, SRJ_SEL_INCREASING, SRJ_SEL_FIXED, SRJ_SEL_MLP = range(4)
 SRJ_PREC_F64, SRJ_PREC_F32, SRJ_PREC_MIXED = range(3)
-SRJ_TOL_REL, SRJ_TOL_ABS = range(2)
+SRJ_TOL_REL, SRJ_TOL_ABS, SRJ_TOL_DINF = range(3)
+SRJ_BC_DIRICHLET, SRJ_BC_NEUMANN = range(2)
 
 # every entry point include/srj.h declares
 EXPORTS = ["srj_version", "srj_level_m", "srj_scheme_omegas", "srj_create", "srj_solve",
@@ -29,7 +30,8 @@ EXPORTS = ["srj_version", "srj_level_m", "srj_scheme_omegas", "srj_create", "srj
 
 
 class srj_grid(C.Structure):
-    _fields_ = [("dim", C.c_int32), ("n", C.c_int64 * 3), ("h", C.c_double * 3)]
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int64 * 3), ("h", C.c_double * 3),
+                ("bc", C.c_int32 * 3)]
 
 
 class srj_stencil(C.Structure):
@@ -135,22 +137,24 @@ def srj_scheme_omegas(level: int):
     return out[:m].copy()
 
 
-def _grid(n, h=None):
+def _grid(n, h=None, bc=None):
     g = srj_grid()
     g.dim = len(n)
     for a in range(3):
         g.n[a] = int(n[a]) if a < len(n) else 1
         g.h[a] = float(h[a]) if (h is not None and a < len(n)) else 0.0
+        g.bc[a] = int(bc[a]) if (bc is not None and a < len(n)) else SRJ_BC_DIRICHLET
     return g
 
 
 def srj_create(n, h=None, eps=None, k_ptr=None, selector=SRJ_SEL_HEURISTIC,
                precision=SRJ_PREC_F64, tol_kind=SRJ_TOL_REL, level0=0, fixed_level=0,
                max_level=0, temporal_depth=0, trace_capacity=0, max_sweeps=0, inner_tol=0.0,
-               stream=None):
-    """Returns an opaque handle (int).  ``k_ptr`` is a device pointer (int) or None."""
+               stream=None, bc=None):
+    """Returns an opaque handle (int).  ``k_ptr`` is a device pointer (int) or None;
+    ``bc`` lists SRJ_BC_* per axis (None: Dirichlet)."""
     L = load()
-    g = _grid(n, h)
+    g = _grid(n, h, bc)
     st = srj_stencil()
     for a in range(3):
         st.eps[a] = float(eps[a]) if (eps is not None and a < len(eps)) else 0.0
