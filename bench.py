@@ -31,12 +31,12 @@ METRIC = ("GLUP/s (% HBM roofline) and time to 1e-8 rel. residual, learned/mixed
 UNIT = "GLUP/s"
 SIDE = 4096
 TOL = 1e-8
-# FP32 instructions per grid-point update of the FP32-pair relaxation (2D,
-# constant coefficients; df_t2d + df_axpy in csrc/df32.cuh): five Knuth
-# two-sums (6 each), three FMA two-products (2 each), two low-part FMAs and
-# ten plain low-part adds for t (48); then one two-product, one FMA, one
-# two-sum, two adds and one Dekker renormalisation (3) for u + omega t (14).
-DF_OPS_PER_LUP = 62
+# FP32 instructions per grid-point update of the FP32-pair relaxation of the
+# isotropic 2D workload (df_t2d_iso + df_axpy in csrc/df32.cuh): five Knuth
+# two-sums (6 each), one exact scaling by 1/4, one FMA and eight plain
+# low-part adds for t (40); then one two-product, one FMA, one two-sum, two
+# adds and one Dekker renormalisation (3) for u + omega t (14).
+DF_OPS_PER_LUP = 54
 WORKLOAD = ("2D Poisson 5-point, 4096x4096 interior, zero Dirichlet, f~U[-1,1] (seed 0+rank), "
             "u0=0, rel residual 1e-8, SRJ scheme family + Alg. 1 heuristic")
 

@@ -113,6 +113,17 @@ typedef struct srj_stencil {
                         (n0+2)(n1+2)(n2+2) doubles (axes >= dim count 1), x
                         fastest, all entries finite and > 0.  Read only during
                         srj_create (face coefficients are derived there). */
+    const double *a_diag;   /* NULL, or an explicit symmetric operator replacing the
+                               PDE stencil (Sec. 4.1: random symmetric diagonally
+                               dominant tridiagonal systems; any dimension):
+                               DEVICE array of the n0*n1*n2 diagonal entries A_pp,
+                               x fastest, all finite and nonzero.  h, eps and k
+                               are then unused (k must be NULL); Dirichlet axes
+                               only.  Read only during srj_create. */
+    const double *a_off[3]; /* with a_diag: DEVICE arrays (grid size, x fastest) of
+                               the couplings A_(p,p+e_a) = A_(p+e_a,p) along each
+                               axis a < dim; the entry of a point whose +e_a
+                               neighbour lies outside the grid is not read. */
 } srj_stencil;
 
 typedef struct srj_opts {
@@ -161,8 +172,9 @@ int32_t srj_scheme_omegas(int32_t level, double *omega_out, int32_t capacity);
  * cudaStream_t (NULL = legacy default stream).  Allocates the device
  * workspace (about 3-6 arrays of the grid size) and the scheme tables on the
  * current device.  On failure *out is NULL and the status says why: a Neumann
- * axis or SRJ_TOL_DINF together with SRJ_PREC_MIXED or variable coefficients
- * gives SRJ_EUNSUPPORTED, a Neumann axis with fewer than 2 points SRJ_EINVAL. */
+ * axis or SRJ_TOL_DINF together with SRJ_PREC_MIXED, variable coefficients or
+ * an explicit operator gives SRJ_EUNSUPPORTED; a Neumann axis with fewer than
+ * 2 points, or both k and a_diag, SRJ_EINVAL. */
 srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil,
                       const srj_opts *opts, void *stream, srj_handle **out);
 

@@ -42,7 +42,8 @@ def build(force: bool = False) -> str:
 
 class _Problem(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_long * 3), ("h", C.c_double * 3),
-                ("eps", C.c_double * 3), ("k", C.POINTER(C.c_double)), ("bc", C.c_int * 3)]
+                ("eps", C.c_double * 3), ("k", C.POINTER(C.c_double)), ("bc", C.c_int * 3),
+                ("adiag", C.POINTER(C.c_double)), ("aoff", C.POINTER(C.c_double) * 3)]
 
 
 def lib():
@@ -96,7 +97,9 @@ class Problem:
     """Structured-grid problem A u = f.
 
     ``n`` lists sizes per axis with x first (x varies fastest in the flattened
-    arrays).  ``bc`` per axis: 0 zero Dirichlet (n interior points), 1
+    arrays).  ``adiag`` / ``aoff`` (one array per axis), when given, define an
+    explicit symmetric operator instead (A_pp = adiag[p], A_{p,p+e_a} =
+    A_{p+e_a,p} = aoff[a][p]; Sec. 4.1's random tridiagonal systems).  ``bc`` per axis: 0 zero Dirichlet (n interior points), 1
     homogeneous Neumann by a mirrored ghost node (n nodes including both ends,
     Sec. 4.2.2); default all Dirichlet.  ``h`` defaults to the unit domain,
     1/(n+1) on a Dirichlet axis and 1/(n-1) on a Neumann axis, ``eps`` to 1 per
@@ -104,8 +107,11 @@ class Problem:
     ``n`` i.e. (..., n1+2, n0+2)) to None (constant).
     """
 
-    def __init__(self, n, h=None, eps=None, k=None, bc=None):
+    def __init__(self, n, h=None, eps=None, k=None, bc=None, adiag=None, aoff=None):
         n = [int(v) for v in n]
+        # explicit symmetric operator: A_pp = adiag[p], A_{p,p+e_a} = aoff[a][p]
+        self.adiag = None if adiag is None else _f64(adiag).ravel()
+        self.aoff = None if aoff is None else [_f64(v).ravel() for v in aoff]
         self.dim = len(n)
         self.n = n
         self.bc = [0] * self.dim if bc is None else [int(v) for v in bc]
@@ -127,6 +133,10 @@ class Problem:
         s.k = _dp(self.k) if self.k is not None else C.POINTER(C.c_double)()
         for a in range(3):
             s.bc[a] = self.bc[a] if a < self.dim else 0
+        if self.adiag is not None:
+            s.adiag = _dp(self.adiag)
+            for a in range(self.dim):
+                s.aoff[a] = _dp(self.aoff[a])
         self._keep = s
         return C.byref(s)
 

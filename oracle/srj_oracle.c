@@ -144,6 +144,13 @@ typedef struct {
     int bc[3];       /* per axis: 0 zero Dirichlet, 1 homogeneous Neumann by a
                         mirrored ghost node (Sec. 4.2.2): u_{-1} = u_1,
                         u_n = u_{n-2}, the grid points including both ends */
+    /* Explicit symmetric operator (Sec. 4.1, random symmetric diagonally
+     * dominant tridiagonal systems, extended to 2D/3D five/seven-point
+     * patterns): when adiag is not NULL, A_pp = adiag[p] and
+     * A_{p,p+e_a} = A_{p+e_a,p} = aoff[a][p]; entries coupling to a point
+     * outside the grid are ignored; h, eps, k and bc are not used. */
+    const double *adiag;
+    const double *aoff[3];
 } oracle_problem;
 
 static long or_npts(const oracle_problem *P)
@@ -192,9 +199,16 @@ static double or_neighbour(const oracle_problem *P, const double *u,
     return u[i + s * stride];
 }
 
+/* linear index of point p (x fastest) */
+static long or_index(const oracle_problem *P, const long p[3])
+{
+    return p[0] + P->n[0] * (p[1] + (P->dim > 1 ? P->n[1] : 1) * p[2]);
+}
+
 /* diagonal entry D_p of A (Sec. 2, splitting A = D + L + U) */
 static double or_diag(const oracle_problem *P, const long p[3])
 {
+    if (P->adiag) return P->adiag[or_index(P, p)];
     double d = 0.0;
     for (int a = 0; a < P->dim; ++a) {
         const double c = P->eps[a] / (P->h[a] * P->h[a]);
@@ -208,6 +222,16 @@ static double or_apply_at(const oracle_problem *P, const double *u,
                           const long p[3], long i)
 {
     double acc = 0.0;
+    if (P->adiag) {
+        acc = P->adiag[i] * u[i];
+        for (int a = 0; a < P->dim; ++a) {
+            long stride = 1;
+            for (int b = 0; b < a; ++b) stride *= P->n[b];
+            if (p[a] + 1 < P->n[a]) acc += P->aoff[a][i] * u[i + stride];
+            if (p[a] > 0) acc += P->aoff[a][i - stride] * u[i - stride];
+        }
+        return acc;
+    }
     for (int a = 0; a < P->dim; ++a) {
         const double c = P->eps[a] / (P->h[a] * P->h[a]);
         for (int s = -1; s <= 1; s += 2)

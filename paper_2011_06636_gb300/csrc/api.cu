@@ -613,10 +613,16 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
             neu |= 1 << a;
         }
     }
+    const bool expl = stencil && stencil->a_diag;
+    if (expl) {
+        if (stencil->k) return SRJ_EINVAL;
+        for (int a = 0; a < grid->dim; ++a)
+            if (!stencil->a_off[a]) return SRJ_EINVAL;
+    }
     if (neu || (opts && opts->tol_kind == SRJ_TOL_DINF)) {
         // mirrored ghosts and the per-sweep change test live in the one-sweep
         // pass kernel, for constant coefficients and one-level arithmetic
-        if ((stencil && stencil->k) || (opts && opts->precision == SRJ_PREC_MIXED))
+        if ((stencil && (stencil->k || expl)) || (opts && opts->precision == SRJ_PREC_MIXED))
             return SRJ_EUNSUPPORTED;
     }
     h = new (std::nothrow) srj_handle();
@@ -674,7 +680,7 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
     g.plane = g.pitch * g.ny;
     h->npts = (long long)g.nx * g.ny * g.nz;
     h->padded = g.plane * g.nz;
-    h->vark = stencil && stencil->k;
+    h->vark = stencil && (stencil->k || stencil->a_diag);
 
     // scheme tables
     std::vector<double> w(kTotalOmegas);
@@ -767,9 +773,17 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
             ck(cudaMemsetAsync(p, 0, h->padded * 8, s), "memset");
         for (void *p : {(void *)h->wx32, (void *)h->wy32, (void *)h->wz32, (void *)h->invd32})
             ck(cudaMemsetAsync(p, 0, h->padded * 4, s), "memset");
-        ck(vark_faces_launch(g, stencil->k, h->wx64, h->wy64, h->wz64, h->invd64, h->wx32,
-                             h->wy32, h->wz32, h->invd32, s),
-           "face weights");
+        if (stencil->a_diag) {
+            const double *aoff[3] = {stencil->a_off[0], g.dim > 1 ? stencil->a_off[1] : nullptr,
+                                     g.dim > 2 ? stencil->a_off[2] : nullptr};
+            ck(explicit_faces_launch(g, stencil->a_diag, aoff, h->wx64, h->wy64, h->wz64,
+                                     h->invd64, h->wx32, h->wy32, h->wz32, h->invd32, s),
+               "explicit operator");
+        } else {
+            ck(vark_faces_launch(g, stencil->k, h->wx64, h->wy64, h->wz64, h->invd64, h->wx32,
+                                 h->wy32, h->wz32, h->invd32, s),
+               "face weights");
+        }
     }
     ck(cudaEventCreate(&h->ev0), "event");
     ck(cudaEventCreate(&h->ev1), "event");
@@ -909,7 +923,8 @@ srj_status srj_create_batched(int32_t nprob, const srj_grid *grids, const srj_st
     if (o.temporal_depth != 0 && o.temporal_depth != 2 && o.temporal_depth != 4)
         return SRJ_EINVAL;
     for (int p = 0; p < nprob; ++p) {
-        if (grids[p].dim != 2 || (stencils && stencils[p].k) || grids[p].bc[0] || grids[p].bc[1])
+        if (grids[p].dim != 2 || (stencils && (stencils[p].k || stencils[p].a_diag)) ||
+            grids[p].bc[0] || grids[p].bc[1])
             return SRJ_EUNSUPPORTED;
         if (grids[p].n[0] < 1 || grids[p].n[1] < 1 || grids[p].n[0] > (1 << 20) ||
             grids[p].n[1] > (1 << 20))

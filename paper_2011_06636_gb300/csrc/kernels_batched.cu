@@ -49,7 +49,8 @@ __device__ double outer_item(const BatchProb &P, int x0, int x1, int y0, int y1,
             const double uyp = y + 1 < g.ny ? P.u[i + g.nx] : 0.0;
             const double Au = g.cx * ((uc - uxm) + (uc - uxp)) + g.cy * ((uc - uym) + (uc - uyp));
             const double r = P.f[i] - Au;
-            ((float *)P.inner.f)[(long long)y * g.pitch + x] = (float)r;
+            // scaled by D^-1: the FP32-pair sweeps read D^-1 f
+            ((float *)P.inner.f)[(long long)y * g.pitch + x] = (float)(r / g.diag);
             acc = fma(r, r, acc);
         }
     }

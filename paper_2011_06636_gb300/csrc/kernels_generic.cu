@@ -293,7 +293,45 @@ __global__ void vark_faces_kernel(GridGeo g, const double *k, double *wx, double
     }
 }
 
+// Explicit symmetric operator: the sweep and residual kernels read it in
+// the same form as face weights (A u)_p = u_p / invd_p - sum_q w_q u_q.
+__global__ void explicit_faces_kernel(GridGeo g, const double *adiag, const double *ax,
+                                      const double *ay, const double *az, double *wx,
+                                      double *wy, double *wz, double *invd, float *wx32,
+                                      float *wy32, float *wz32, float *invd32) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long x = i % g.nx, yz = i / g.nx;
+        const long long y = yz % g.ny, z = yz / g.ny;
+        const double fx = x + 1 < g.nx ? -ax[i] : 0.0;
+        const double fy = (g.dim > 1 && y + 1 < g.ny) ? -ay[i] : 0.0;
+        const double fz = (g.dim > 2 && z + 1 < g.nz) ? -az[i] : 0.0;
+        const double id = 1.0 / adiag[i];
+        const long long p = x + g.pitch * y + g.plane * z;
+        wx[p] = fx;
+        wy[p] = fy;
+        wz[p] = fz;
+        invd[p] = id;
+        wx32[p] = (float)fx;
+        wy32[p] = (float)fy;
+        wz32[p] = (float)fz;
+        invd32[p] = (float)id;
+    }
+}
+
 }  // namespace
+
+cudaError_t explicit_faces_launch(const GridGeo &g, const double *adiag,
+                                  const double *const *aoff, double *wx, double *wy,
+                                  double *wz, double *invd, float *wx32, float *wy32,
+                                  float *wz32, float *invd32, cudaStream_t s) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    explicit_faces_kernel<<<stream_blocks(n), 256, 0, s>>>(g, adiag, aoff[0], aoff[1], aoff[2],
+                                                           wx, wy, wz, invd, wx32, wy32, wz32,
+                                                           invd32);
+    return cudaGetLastError();
+}
 
 cudaError_t vark_faces_launch(const GridGeo &g, const double *k, double *wx, double *wy,
                               double *wz, double *invd, float *wx32, float *wy32, float *wz32,
@@ -344,7 +382,9 @@ __global__ void __launch_bounds__(kBlock) outer_residual_kernel(OuterArgs a) {
             if (DIM > 2) Au += g.cz * ((uc - uzm) + (uc - uzp));
         }
         const double r = a.f[i] - Au;
-        a.r32[pp] = (float)r;
+        // the FP32-pair sweeps read a constant-coefficient right-hand side
+        // scaled by D^-1 (one rounding either way)
+        a.r32[pp] = VARK ? (float)r : (float)(r / g.diag);
         part += r * r;
     }
     const double tot = block_sum(part);

@@ -97,7 +97,7 @@ extern "C" srj_status srj_residual_norm_noalloc(const srj_grid *grid, const srj_
                                                 void *stream) {
     if (!grid || !f || !u || !out) return SRJ_EINVAL;
     if (grid->dim < 1 || grid->dim > 3) return SRJ_EINVAL;
-    if (stencil && stencil->k) return SRJ_EUNSUPPORTED;
+    if (stencil && (stencil->k || stencil->a_diag)) return SRJ_EUNSUPPORTED;
     for (int a = 0; a < grid->dim; ++a)
         if (grid->bc[a] != SRJ_BC_DIRICHLET) return SRJ_EUNSUPPORTED;
     long long n[3] = {1, 1, 1};

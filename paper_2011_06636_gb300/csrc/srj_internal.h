@@ -226,6 +226,13 @@ cudaError_t copy_in_launch(int prec, const GridGeo &g, const void *dense, void *
 cudaError_t copy_out_launch(int prec, const GridGeo &g, const DevState *st, void *const *pads,
                             void *dense, cudaStream_t s);
 
+// Face weights of an explicit symmetric operator (kernels_generic.cu):
+// w_a = -A_(p,p+e_a) (zero where the neighbour is outside), invd = 1 / A_pp.
+cudaError_t explicit_faces_launch(const GridGeo &g, const double *adiag,
+                                  const double *const *aoff, double *wx, double *wy,
+                                  double *wz, double *invd, float *wx32, float *wy32,
+                                  float *wz32, float *invd32, cudaStream_t s);
+
 // Face weights of the variable-coefficient operator (kernels_generic.cu).
 cudaError_t vark_faces_launch(const GridGeo &g, const double *k, double *wx,
                               double *wy, double *wz, double *invd,

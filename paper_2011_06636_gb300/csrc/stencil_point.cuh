@@ -95,16 +95,19 @@ struct Point {
     }
 
     // constant coefficients: t = a_x (u_-x + u_+x) + ... + D^-1 f - u_c with
-    // a = c / D, written as the cheaper sum-then-scale form.
+    // a = c / D, written as the cheaper sum-then-scale form.  The FP32-pair
+    // state takes its right-hand side already scaled, f = D^-1 f (the
+    // mixed-precision outer residual stores it so; invd is then unused).
     __device__ __forceinline__ static T t_const(const T *nb, const C *a, C invd, C f, T uc) {
         if constexpr (PREC == PREC_DF) {
+            (void)invd;
             if constexpr (DIM == 2) {
-                return df_t2d(nb[0], nb[1], nb[2], nb[3], a[0], a[1], invd, f, uc);
+                return df_t2d(nb[0], nb[1], nb[2], nb[3], a[0], a[1], f, uc);
             } else {
                 df32 s = df_mul_f(df_add(nb[0], nb[1]), a[0]);
                 if (DIM > 1) s = df_add(s, df_mul_f(df_add(nb[2], nb[3]), a[1]));
                 if (DIM > 2) s = df_add(s, df_mul_f(df_add(nb[4], nb[5]), a[2]));
-                s = df_add(s, df_two_prod(invd, f));
+                s = df_add_f(s, f);
                 return df_sub(s, uc);
             }
         } else {
@@ -113,6 +116,12 @@ struct Point {
             if (DIM > 2) s += a[2] * (nb[4] + nb[5]);
             return s + invd * f - uc;
         }
+    }
+
+    // 2D isotropic FP32-pair case a_x = a_y = 1/4 (scaled right-hand side)
+    __device__ __forceinline__ static T t_const_iso(const T *nb, C f, T uc) {
+        static_assert(PREC == PREC_DF && DIM == 2, "isotropic form: 2D FP32 pair only");
+        return df_t2d_iso(nb[0], nb[1], nb[2], nb[3], f, uc);
     }
 
     __device__ __forceinline__ static T relax(T uc, T t, double omega) {

@@ -23,6 +23,14 @@ Recipes (the paper uses no dataset; every workload is synthetic):
   the others the anisotropic operator -eps u_xx - u_yy with eps log-uniform in
   [1e-2, 1]; f i.i.d. N(0, 1).
 * The paper's own experiments: b = 1 (Sec. 3, Sec. 4.1) and f = 1 (Sec. 4.2.3).
+* Random symmetric diagonally dominant tridiagonal matrices (Sec. 4.1):
+  diagonal d_i ~ U[0, 1), off-diagonal e_i = -U[0, 1) (the same array above
+  and below the diagonal; the sign follows the 1D Poisson matrix, and a
+  diagonal +-1 similarity shows it does not change Jacobi or SRJ
+  convergence); every row that is not diagonally dominant gets
+  |d_i| = |e_(i-1)| + |e_i|; then d_0 = 2 |e_0| and d_(N-1) = 2 |e_(N-2)|.
+* Laplace with Neumann boundaries (Sec. 4.2.2): f = 0, u0 i.i.d.
+  uniform[-1, 1].
 * Learned selector: initial weights He-uniform (limit sqrt(6 / fan_in)), zero
   biases, parameter order W1 (64x12), b1, W2 (64x64), b2, W3 (25x64), b3; the
   minibatch order of training is a seeded permutation per epoch.
@@ -105,6 +113,25 @@ def batched_problems(count: int = 256, seed: int = 0, smin: int = 64,
         out.append(dict(n=[int(sides[i]), int(sides[i])], eps=[e, 1.0],
                         seed_f=int(seed * 100003 + i)))
     return out
+
+
+def random_sdd_tridiagonal(N: int, seed: int):
+    """(diag, off) of a random symmetric diagonally dominant tridiagonal
+    matrix of order N by the recipe of Sec. 4.1 (module docstring): A_ii =
+    diag[i], A_(i,i+1) = A_(i+1,i) = off[i] (off has N entries, the last
+    unused)."""
+    rng = np.random.default_rng(seed)
+    d = rng.random(N)
+    e = -rng.random(N)
+    e[N - 1] = 0.0
+    left = np.concatenate([[0.0], np.abs(e[:N - 1])])
+    right = np.abs(e)
+    need = left + right
+    d = np.where(np.abs(d) < need, need, d)
+    if N >= 2:
+        d[0] = 2.0 * abs(e[0])
+        d[N - 1] = 2.0 * abs(e[N - 2])
+    return d, e
 
 
 MLP_SHAPES = [(64, 12), (64,), (64, 64), (64,), (25, 64), (25,)]

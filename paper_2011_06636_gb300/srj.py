@@ -35,7 +35,8 @@ class srj_grid(C.Structure):
 
 
 class srj_stencil(C.Structure):
-    _fields_ = [("eps", C.c_double * 3), ("k", C.c_void_p)]
+    _fields_ = [("eps", C.c_double * 3), ("k", C.c_void_p), ("a_diag", C.c_void_p),
+                ("a_off", C.c_void_p * 3)]
 
 
 class srj_opts(C.Structure):
@@ -150,15 +151,19 @@ def _grid(n, h=None, bc=None):
 def srj_create(n, h=None, eps=None, k_ptr=None, selector=SRJ_SEL_HEURISTIC,
                precision=SRJ_PREC_F64, tol_kind=SRJ_TOL_REL, level0=0, fixed_level=0,
                max_level=0, temporal_depth=0, trace_capacity=0, max_sweeps=0, inner_tol=0.0,
-               stream=None, bc=None):
+               stream=None, bc=None, a_diag_ptr=None, a_off_ptrs=None):
     """Returns an opaque handle (int).  ``k_ptr`` is a device pointer (int) or None;
-    ``bc`` lists SRJ_BC_* per axis (None: Dirichlet)."""
+    ``bc`` lists SRJ_BC_* per axis (None: Dirichlet); ``a_diag_ptr`` and
+    ``a_off_ptrs`` (device pointers) give an explicit symmetric operator."""
     L = load()
     g = _grid(n, h, bc)
     st = srj_stencil()
     for a in range(3):
         st.eps[a] = float(eps[a]) if (eps is not None and a < len(eps)) else 0.0
     st.k = k_ptr
+    st.a_diag = a_diag_ptr
+    for a, p in enumerate(a_off_ptrs or []):
+        st.a_off[a] = p
     o = srj_opts(selector, precision, tol_kind, level0, fixed_level, max_level, temporal_depth,
                  trace_capacity, max_sweeps, inner_tol)
     hnd = C.c_void_p()
