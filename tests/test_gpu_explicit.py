@@ -79,7 +79,12 @@ def test_random_tridiagonal_matches_oracle(S, orc, N, seed, rule):
     np.testing.assert_array_equal(lv, ref["levels"])
     assert st["sweeps"] == ref["sweeps"]
     np.testing.assert_allclose(u, ref["u"], rtol=0, atol=1e-10 * np.abs(ref["u"]).max())
-    np.testing.assert_allclose(rn, ref["rns"], rtol=1e-9, atol=1e-13 * ref["r0"])
+    # evaluating f - A u loses about eps || |A| |u| || to cancellation, and the
+    # two iterates carry independent rounding: the per-cycle norms agree to
+    # that scale (64 eps of it), not relative to a tiny late-cycle norm
+    absA = orc.Problem([N], adiag=np.abs(d), aoff=[np.abs(e)])
+    floor = np.linalg.norm(orc.apply_A(absA, np.abs(ref["u"])))
+    np.testing.assert_allclose(rn, ref["rns"], rtol=1e-9, atol=64 * 2.0 ** -52 * floor)
 
 
 @pytest.mark.parametrize("n", [[70, 45], [33, 20, 17]])
