@@ -25,7 +25,12 @@
 namespace srj {
 namespace {
 
-constexpr int kBW = kWaveWarps;
+// Warps per CTA: 6 for T = 2 (the FP32-pair item needs about 160 registers
+// to keep its update chains without recomputation; see kernels_wave2d.cu).
+template <int T>
+__host__ __device__ constexpr int batch_warps() {
+    return T == 2 ? 6 : kWaveWarps;
+}
 
 enum BatchPhase : int32_t { BPH_OUTER = 0, BPH_INNER = 1, BPH_UPDATE = 2, BPH_DONE = 3 };
 
@@ -148,9 +153,10 @@ __device__ void finalize_problem(const BatchLaunch &b, int p, const PassPlan &pl
 }
 
 template <int T>
-__global__ void __launch_bounds__(32 * kBW, (batch_min_blocks<T>()))
+__global__ void __launch_bounds__(32 * batch_warps<T>(), (batch_min_blocks<T>()))
     batched_kernel(BatchLaunch b) {
     using W = Wave<PREC_DF, T>;
+    constexpr int kBW = batch_warps<T>();
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile unsigned int *)b.ndone >=
@@ -216,8 +222,10 @@ static void *batched_entry(int T) {
     return T >= 4 ? (void *)&batched_kernel<4> : (void *)&batched_kernel<2>;
 }
 
+static int batched_warps(int T) { return T >= 4 ? batch_warps<4>() : batch_warps<2>(); }
+
 int batched_smem(int T) {
-    return kBW * (T >= 4 ? Wave<PREC_DF, 4>::SMEM_WARP : Wave<PREC_DF, 2>::SMEM_WARP);
+    return batched_warps(T) * (T >= 4 ? Wave<PREC_DF, 4>::SMEM_WARP : Wave<PREC_DF, 2>::SMEM_WARP);
 }
 
 int batched_grid(int T, int num_sms) { return num_sms * (T >= 4 ? 1 : 2); }
@@ -229,7 +237,8 @@ cudaError_t batched_prepare(int T) {
 
 cudaError_t batched_launch(int T, int num_sms, const BatchLaunch &b, cudaStream_t s) {
     void *args[] = {(void *)&b};
-    return cudaLaunchKernel(batched_entry(T), dim3(batched_grid(T, num_sms)), dim3(32 * kBW),
+    return cudaLaunchKernel(batched_entry(T), dim3(batched_grid(T, num_sms)),
+                            dim3(32 * batched_warps(T)),
                             args, batched_smem(T), s);
 }
 
@@ -238,7 +247,7 @@ cudaError_t add_batched_node(int T, int num_sms, const BatchLaunch &b, cudaGraph
     cudaKernelNodeParams kp{};
     kp.func = batched_entry(T);
     kp.gridDim = dim3(batched_grid(T, num_sms));
-    kp.blockDim = dim3(32 * kBW);
+    kp.blockDim = dim3(32 * batched_warps(T));
     kp.sharedMemBytes = batched_smem(T);
     kp.kernelParams = args;
     cudaGraphNode_t node;

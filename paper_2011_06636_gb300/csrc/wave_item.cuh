@@ -288,7 +288,9 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
             if (CHK && t < 3 * s) continue;           // above every needed row
             if (CHK && t > nload - 1 + s) continue;   // below every needed row
             const int row = jt - dir * (2 * s);
-            if (s > c.nsw) {  // identity level (last pass of a cycle)
+            // identity level: only in the last pass of a cycle (a pass without
+            // the residual always runs all T sweeps)
+            if (RESID && s > c.nsw) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) ring[s][S3][v] = ring[s - 1][S2][v];
                 continue;
@@ -323,7 +325,7 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
         // output: level T's new row j(t) - 2T dir
         {
             const int row = jt - dir * (2 * T);
-            if (c.nsw > 0 && row >= y0 && row < y1) {
+            if ((!RESID || c.nsw > 0) && row >= y0 && row < y1) {
                 const long long base = (long long)row * c.pitch + col0;
                 if (W::VEC_OUT && whole_lane) {  // one 16-byte store per array
                     if constexpr (LO) {
