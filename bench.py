@@ -306,6 +306,29 @@ def batched_leg(srj, inputs, torch, stream, seed=0, count=256, fp64=True):
     return out
 
 
+# ------------------------------------------------------------------- multigrid
+def mg_leg(srj, inputs, torch, stream, seed=0, side=4095):
+    """Multigrid with SRJ smoothing on the 2D Poisson problem of the headline
+    (4095^2: n = 2^k - 1 for the hierarchy), f ~ U[-1,1], rel 1e-8, FP64:
+    the SRJ level-1 smoother (M = 2) and the classic damped Jacobi (level 0,
+    omega = 2/3), both V(1,1)."""
+    n = [side, side]
+    f = torch.as_tensor(inputs.uniform_rhs(n, seed=seed).ravel(), device="cuda")
+    out = {"grid": n, "tol": TOL}
+    for label, lv in (("srj_level1_smoother", 1), ("damped_jacobi_smoother", 0)):
+        h = srj.srj_mg_create(n, smoother_level=lv, stream=stream.cuda_stream)
+        u = torch.zeros_like(f)
+        srj.srj_mg_solve(h, f.data_ptr(), u.data_ptr(), TOL)  # warm-up (graph capture)
+        u.zero_()
+        st = srj.srj_mg_solve(h, f.data_ptr(), u.data_ptr(), TOL)
+        srj.srj_destroy(h)
+        out[label] = {"time_to_tol_s": st["seconds"], "vcycles": st["cycles"],
+                      "fine_sweeps": st["sweeps"], "kernel_launches": st["passes"],
+                      "rel_residual": st["rn"] / st["r0"],
+                      "status": srj.STATUS_NAMES[st["status"]]}
+    return out
+
+
 # ----------------------------------------------------------- learned selector
 def selector_leg(srj, inputs, torch, stream, seed=0):
     """Unseen problems for the learned selector: 2D anisotropic (eps_x = 0.01)
@@ -517,6 +540,10 @@ def run_ours(args, rank, world):
     sel = None
     if not args.no_selector:
         sel = selector_leg(srj, inputs, torch, stream, seed=rank)
+    mg = None
+    if not args.no_mg:
+        mg = mg_leg(srj, inputs, torch, stream, seed=rank)
+        mg["srj_mixed_4096_time_to_tol_s"] = ms_max / args.steps / 1e3
     vark = None
     if args.with_3d:
         vark = vark3d_leg(srj, inputs, torch, stream, seed=rank, side=args.side3d,
@@ -561,6 +588,7 @@ def run_ours(args, rank, world):
             "fp32_sweeps": f32,
             "batched": batched,
             "learned_selector": sel,
+            "multigrid_srj_smoother": mg,
             "vark3d": vark,
             "mixed_vs_plain_speedup": (fp64["time_to_tol_s"] / (ms_max / args.steps / 1e3))
             if fp64 else None,
@@ -582,6 +610,7 @@ def main():
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-selector", action="store_true")
+    ap.add_argument("--no-mg", action="store_true", help="skip the multigrid leg")
     ap.add_argument("--with-3d", action="store_true", help="add the 3D variable-k leg")
     ap.add_argument("--side3d", type=int, default=512)
     ap.add_argument("--f32-depth", type=int, default=0, help="temporal depth of the FP32 leg")

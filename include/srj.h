@@ -290,6 +290,38 @@ srj_status srj_residual_norm_noalloc(const srj_grid *grid, const srj_stencil *st
                                      const double *f, const double *u, double *out,
                                      void *stream);
 
+/* Geometric multigrid with SRJ smoothing -- an adjacent use of the method:
+ * Sec. 1 names Jacobi iteration as the usual multigrid smoother and Sec. 5
+ * names SRJ schemes as smoothers that accelerate multigrid.  V-cycles of:
+ * nu1 SRJ cycles of scheme level smoother_level (its M(level) factors of Sec. 2,
+ * Eq. srj-relaxation-parameters, in the library's order) as pre-smoother, the
+ * residual, full-weighting restriction to the grid with (n - 1) / 2 points
+ * and twice the spacing per axis (operator rediscretised), the coarse
+ * correction by recursion down to one point (solved exactly), linear
+ * interpolation of the correction, nu2 cycles as post-smoother.  All FP64.
+ * Level 0 (M = 1, omega = 2/3) is the classic damped-Jacobi smoother. */
+typedef struct srj_mg_opts {
+    int32_t smoother_level; /* scheme level of the smoother, 0..24 (default 1) */
+    int32_t nu1, nu2;       /* pre- and post-smoothing cycles (0 means 1 each) */
+    int32_t max_cycles;     /* V-cycle cap (0 means 100) */
+} srj_mg_opts;
+
+/* Create a multigrid solver.  grid: every axis n = 2^k - 1 with the same k
+ * (k >= 1), zero Dirichlet (SRJ_EINVAL otherwise); stencil NULL or constant
+ * coefficients eps (k or a_diag give SRJ_EUNSUPPORTED).  opts may be NULL.
+ * Allocates about 4 arrays of every grid of the hierarchy (4/3 to 8/7 of the
+ * fine grid's 4 arrays) on the current device. */
+srj_status srj_mg_create(const srj_grid *grid, const srj_stencil *stencil,
+                         const srj_mg_opts *opts, void *stream, srj_handle **out);
+
+/* V-cycles on A u = f until ||f - A u|| / ||f - A u0|| < tol.  f, u: DEVICE
+ * dense FP64 arrays of the fine grid (u: u0 in, solution out).  stats (HOST,
+ * may be NULL): cycles = V-cycles, sweeps = fine-grid relaxed Jacobi sweeps,
+ * passes = kernel launches, r0, rn, seconds.  SRJ_ENOTCONV after max_cycles.
+ * The handle must come from srj_mg_create (SRJ_EINVAL otherwise). */
+srj_status srj_mg_solve(srj_handle *h, const double *f, double *u, double tol,
+                        srj_stats *stats);
+
 /* Text describing the last failure on h (static storage inside h), or a
  * generic text for h == NULL. */
 const char *srj_last_error(const srj_handle *h);

@@ -81,6 +81,12 @@ def lib():
                                           C.c_long, C.c_long, lp, dp]
         L.oracle_jacobi_solve.restype = C.c_int
         L.oracle_thomas.argtypes = [C.c_long, dp, dp, dp, dp, dp]
+        L.oracle_mg_restrict.argtypes = [pp, dp, pp, dp]
+        L.oracle_mg_prolong_add.argtypes = [pp, dp, pp, dp]
+        L.oracle_mg_vcycle.argtypes = [pp, dp, dp, C.c_int, C.c_int, C.c_int]
+        L.oracle_mg_solve.argtypes = [pp, dp, dp, C.c_double, C.c_int, C.c_int, C.c_int,
+                                      C.c_long, lp, dp, dp, dp]
+        L.oracle_mg_solve.restype = C.c_int
         _lib = L
     return _lib
 
@@ -266,3 +272,43 @@ def thomas(a, b, c, d):
     x = np.zeros(len(b))
     lib().oracle_thomas(len(b), _dp(a), _dp(b), _dp(c), _dp(d), _dp(x))
     return x
+
+
+def mg_coarse(P: Problem) -> Problem:
+    """The next coarser multigrid problem: (n - 1) / 2 points, twice the spacing."""
+    return Problem([(v - 1) // 2 for v in P.n], h=[2 * v for v in P.h], eps=P.eps)
+
+
+def mg_restrict(P: Problem, r):
+    Pc = mg_coarse(P)
+    r = _f64(r).ravel()
+    out = np.zeros(Pc.size)
+    lib().oracle_mg_restrict(P._c(), _dp(r), Pc._c(), _dp(out))
+    return out
+
+
+def mg_prolong_add(Pc: Problem, ec, P: Problem, u):
+    ec = _f64(ec).ravel()
+    u = _f64(u).ravel().copy()
+    lib().oracle_mg_prolong_add(Pc._c(), _dp(ec), P._c(), _dp(u))
+    return u
+
+
+def mg_vcycle(P: Problem, u, f, level=0, nu1=1, nu2=1):
+    u = _f64(u).ravel().copy()
+    f = _f64(f).ravel()
+    lib().oracle_mg_vcycle(P._c(), _dp(u), _dp(f), int(level), int(nu1), int(nu2))
+    return u
+
+
+def mg_solve(P: Problem, f, u0=None, tol=1e-8, level=0, nu1=1, nu2=1, max_cycles=200):
+    f = _f64(f).ravel()
+    u = np.zeros(P.size) if u0 is None else _f64(u0).ravel().copy()
+    cy = C.c_long()
+    r0 = C.c_double()
+    rn = C.c_double()
+    tr = np.zeros(max_cycles)
+    st = lib().oracle_mg_solve(P._c(), _dp(f), _dp(u), float(tol), int(level), int(nu1), int(nu2),
+                               int(max_cycles), C.byref(cy), C.byref(r0), C.byref(rn), _dp(tr))
+    return dict(u=u, status=st, cycles=cy.value, r0=r0.value, rn=rn.value,
+                rns=tr[:cy.value].copy())

@@ -486,3 +486,142 @@ void oracle_thomas(long N, const double *a, const double *b, const double *c,
     free(cp);
     free(dp);
 }
+
+/* ------------------------------------------------------------------------
+ * Geometric multigrid with SRJ smoothing: an adjacent use of the method
+ * (Sec. 1: Jacobi iteration is the usual multigrid smoother; Sec. 5: SRJ
+ * schemes used as smoothers accelerate multigrid).  Textbook V-cycle:
+ * nu1 SRJ cycles of one scheme level as pre-smoother, the residual,
+ * full-weighting restriction to the grid with (n - 1) / 2 points and twice
+ * the spacing per axis (the operator rediscretised there), the coarse
+ * correction by recursion, (bi/tri)linear interpolation of the correction,
+ * nu2 cycles as post-smoother.  On the one-point coarsest grid A u = f is
+ * solved exactly, u = f / D.  Constant coefficients, zero Dirichlet values,
+ * n = 2^k - 1 points on every axis with the same k.
+ * ------------------------------------------------------------------------ */
+static void or_mg_coarse(const oracle_problem *Pf, oracle_problem *Pc)
+{
+    *Pc = *Pf;
+    for (int a = 0; a < Pf->dim; ++a) {
+        Pc->n[a] = (Pf->n[a] - 1) / 2;
+        Pc->h[a] = 2.0 * Pf->h[a];
+    }
+}
+
+/* Full weighting: coarse point c sits on fine point 2c + 1 per axis; its value
+ * is the sum over the 3^dim fine points around it with weight
+ * prod_a (1/2 on the axis of c, 1/4 one step off). */
+void oracle_mg_restrict(const oracle_problem *Pf, const double *rf,
+                        const oracle_problem *Pc, double *fc)
+{
+    const long nf0 = Pf->n[0], nf1 = Pf->dim > 1 ? Pf->n[1] : 1;
+    const int r1 = Pf->dim > 1 ? 1 : 0, r2 = Pf->dim > 2 ? 1 : 0;
+    long i = 0;
+    for (long z = 0; z < or_extent(Pc, 2); ++z)
+        for (long y = 0; y < or_extent(Pc, 1); ++y)
+            for (long x = 0; x < or_extent(Pc, 0); ++x, ++i) {
+                double acc = 0.0;
+                for (int dz = -r2; dz <= r2; ++dz)
+                    for (int dy = -r1; dy <= r1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const long fx = 2 * x + 1 + dx;
+                            const long fy = r1 ? 2 * y + 1 + dy : 0;
+                            const long fz = r2 ? 2 * z + 1 + dz : 0;
+                            double w = dx == 0 ? 0.5 : 0.25;
+                            if (r1) w *= dy == 0 ? 0.5 : 0.25;
+                            if (r2) w *= dz == 0 ? 0.5 : 0.25;
+                            acc += w * rf[fx + nf0 * (fy + nf1 * fz)];
+                        }
+                fc[i] = acc;
+            }
+}
+
+/* Linear interpolation per axis: a fine point 2c + 1 takes the coarse value
+ * c; a fine point 2c takes half of coarse c - 1 and half of coarse c (zero
+ * outside the coarse grid).  The interpolated correction is added to uf. */
+void oracle_mg_prolong_add(const oracle_problem *Pc, const double *ec,
+                           const oracle_problem *Pf, double *uf)
+{
+    const long nc0 = Pc->n[0], nc1 = Pc->dim > 1 ? Pc->n[1] : 1;
+    long i = 0;
+    for (long z = 0; z < or_extent(Pf, 2); ++z)
+        for (long y = 0; y < or_extent(Pf, 1); ++y)
+            for (long x = 0; x < or_extent(Pf, 0); ++x, ++i) {
+                long cx[2], cy[2], cz[2];
+                double wx[2], wy[2], wz[2];
+                int mx, my, mz;
+                /* coarse neighbours and weights per axis */
+                if (x % 2 == 1) { cx[0] = x / 2; wx[0] = 1.0; mx = 1; }
+                else { cx[0] = x / 2 - 1; cx[1] = x / 2; wx[0] = wx[1] = 0.5; mx = 2; }
+                if (Pf->dim < 2) { cy[0] = 0; wy[0] = 1.0; my = 1; }
+                else if (y % 2 == 1) { cy[0] = y / 2; wy[0] = 1.0; my = 1; }
+                else { cy[0] = y / 2 - 1; cy[1] = y / 2; wy[0] = wy[1] = 0.5; my = 2; }
+                if (Pf->dim < 3) { cz[0] = 0; wz[0] = 1.0; mz = 1; }
+                else if (z % 2 == 1) { cz[0] = z / 2; wz[0] = 1.0; mz = 1; }
+                else { cz[0] = z / 2 - 1; cz[1] = z / 2; wz[0] = wz[1] = 0.5; mz = 2; }
+                double acc = 0.0;
+                for (int c = 0; c < mz; ++c)
+                    for (int b = 0; b < my; ++b)
+                        for (int a = 0; a < mx; ++a) {
+                            if (cx[a] < 0 || cx[a] >= nc0) continue;
+                            if (Pf->dim > 1 && (cy[b] < 0 || cy[b] >= nc1)) continue;
+                            if (Pf->dim > 2 && (cz[c] < 0 || cz[c] >= Pc->n[2])) continue;
+                            acc += wx[a] * wy[b] * wz[c] * ec[cx[a] + nc0 * (cy[b] + nc1 * cz[c])];
+                        }
+                uf[i] += acc;
+            }
+}
+
+/* One V-cycle on A u = f (u updated in place). */
+void oracle_mg_vcycle(const oracle_problem *P, double *u, const double *f,
+                      int level, int nu1, int nu2)
+{
+    const long N = or_npts(P);
+    if (N == 1) {
+        const long p[3] = {0, 0, 0};
+        u[0] = f[0] / or_diag(P, p);
+        return;
+    }
+    double omega[2362];
+    const int M = oracle_level_omegas(level, omega);
+    for (int c = 0; c < nu1; ++c) oracle_sweeps(P, u, f, omega, M);
+    double *r = (double *)malloc(sizeof(double) * (size_t)N);
+    oracle_apply_A(P, u, r);
+    for (long i = 0; i < N; ++i) r[i] = f[i] - r[i];
+    oracle_problem Pc;
+    or_mg_coarse(P, &Pc);
+    const long Nc = or_npts(&Pc);
+    double *fc = (double *)malloc(sizeof(double) * (size_t)Nc);
+    double *ec = (double *)calloc((size_t)Nc, sizeof(double));
+    oracle_mg_restrict(P, r, &Pc, fc);
+    oracle_mg_vcycle(&Pc, ec, fc, level, nu1, nu2);
+    oracle_mg_prolong_add(&Pc, ec, P, u);
+    for (int c = 0; c < nu2; ++c) oracle_sweeps(P, u, f, omega, M);
+    free(r);
+    free(fc);
+    free(ec);
+}
+
+/* V-cycles until ||f - A u|| / ||f - A u0|| < tol; rn_trace (may be NULL,
+ * capacity max_cycles) receives the norm after each V-cycle.  Returns 0 when
+ * converged, 1 otherwise. */
+int oracle_mg_solve(const oracle_problem *P, const double *f, double *u, double tol,
+                    int level, int nu1, int nu2, long max_cycles, long *cycles_out,
+                    double *r0_out, double *rn_out, double *rn_trace)
+{
+    const double r0 = oracle_residual_norm(P, u, f);
+    double rn = r0;
+    long c = 0;
+    int status = r0 == 0.0 ? 0 : 1;
+    while (status != 0 && c < max_cycles) {
+        oracle_mg_vcycle(P, u, f, level, nu1, nu2);
+        rn = oracle_residual_norm(P, u, f);
+        if (rn_trace) rn_trace[c] = rn;
+        c += 1;
+        if (rn / r0 < tol) status = 0;
+    }
+    if (cycles_out) *cycles_out = c;
+    if (r0_out) *r0_out = r0;
+    if (rn_out) *rn_out = rn;
+    return status;
+}

@@ -72,6 +72,7 @@ struct srj_handle {
     long long last_cycles = 0;
     std::string err;
     struct BatchData *batch = nullptr;  // srj_create_batched handles only
+    struct MgData *mg = nullptr;        // srj_mg_create handles only
     uint16_t *mlp_w = nullptr;          // learned selector weights (BF16, 6617)
     bool mlp_loaded = false;
 };
@@ -95,6 +96,21 @@ struct BatchData {
     double graph_tol = -1.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+};
+
+// Hierarchy and the captured V-cycle of a multigrid handle.
+struct MgData {
+    int nlev = 0;
+    std::vector<MgGeo> geo;  // level 0 = fine grid
+    std::vector<double *> U0, U1, F, R;
+    std::vector<double> omegas;  // the smoother's factors (one SRJ cycle)
+    int nu1 = 1, nu2 = 1, max_cycles = 100;
+    double *partials = nullptr, *norm2 = nullptr;
+    double *h_norm2 = nullptr;  // pinned
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;  // private stream the V-cycle is captured on
+    long long fine_sweeps = 0, launches = 0;  // per V-cycle
 };
 
 namespace {
@@ -309,7 +325,6 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
     oa.ticket = h->oticket;
     oa.out_norm2 = h->onorm2;
 
-    const int kCarry = 3;  // inner solves restart this many levels below the last one
     const long long kInnerCap = 200000;  // sweeps of one inner solve
     const long long max_sweeps = h->opts.max_sweeps;
     long long sweeps = 0, cycles = 0, passes = 0, outer = 0;
@@ -328,7 +343,7 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
             cycles += r.cycles;
             passes += r.passes;
             final_level = r.level;
-            level = r.level - kCarry > 0 ? r.level - kCarry : 0;
+            level = r.level - kInnerCarry > 0 ? r.level - kInnerCarry : 0;
             trace_base += (int)r.cycles;
             if (r.status == DST_DIVERGED) {
                 result = DST_DIVERGED;
@@ -798,6 +813,7 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
 
 srj_status srj_solve(srj_handle *h, const void *f, void *u, double tol, srj_stats *stats) {
     if (!h) return SRJ_EINVAL;
+    if (h->mg) return fail(h, SRJ_EINVAL, "srj_solve: multigrid handle (use srj_mg_solve)");
     if (h->opts.selector == SRJ_SEL_MLP && !h->mlp_loaded)
         return fail(h, SRJ_EINVAL, "srj_solve: learned selector without weights");
     if (!f || !u || !(tol > 0) || !std::isfinite(tol))
@@ -821,6 +837,7 @@ srj_status srj_solve(srj_handle *h, const void *f, void *u, double tol, srj_stat
 srj_status srj_solve_host(srj_handle *h, const void *f_host, void *u_host, double tol,
                           srj_stats *stats) {
     if (!h) return SRJ_EINVAL;
+    if (h->mg) return fail(h, SRJ_EINVAL, "srj_solve_host: multigrid handle");
     if (h->opts.selector == SRJ_SEL_MLP && !h->mlp_loaded)
         return fail(h, SRJ_EINVAL, "srj_solve_host: learned selector without weights");
     if (!f_host || !u_host) return fail(h, SRJ_EINVAL, "srj_solve_host: null array");
@@ -851,6 +868,7 @@ srj_status srj_solve_host(srj_handle *h, const void *f_host, void *u_host, doubl
 srj_status srj_run_levels(srj_handle *h, const void *f, void *u, const int32_t *levels,
                           int64_t ncycles, double *rn_out) {
     if (!h) return SRJ_EINVAL;
+    if (h->mg) return fail(h, SRJ_EINVAL, "srj_run_levels: multigrid handle");
     if (!f || !u || !levels || ncycles < 1)
         return fail(h, SRJ_EINVAL, "srj_run_levels: bad arguments");
     if (h->user_prec == SRJ_PREC_MIXED)
@@ -881,6 +899,7 @@ srj_status srj_run_levels(srj_handle *h, const void *f, void *u, const int32_t *
 
 srj_status srj_residual_norm(srj_handle *h, const void *f, const void *u, double *out) {
     if (!h) return SRJ_EINVAL;
+    if (h->mg) return fail(h, SRJ_EINVAL, "srj_residual_norm: multigrid handle");
     if (!f || !u || !out) return fail(h, SRJ_EINVAL, "srj_residual_norm: null argument");
     if (h->user_prec == SRJ_PREC_MIXED)
         return fail(h, SRJ_EUNSUPPORTED, "srj_residual_norm: F64 or F32 precision only");
@@ -1058,6 +1077,7 @@ srj_status srj_solve_batched(srj_handle *h, const double *const *f, double *cons
 
 srj_status srj_mlp_set_weights(srj_handle *h, const uint16_t *w, int64_t count) {
     if (!h) return SRJ_EINVAL;
+    if (h->mg) return fail(h, SRJ_EINVAL, "srj_mlp_set_weights: multigrid handle");
     if (!w || count != 6617) return fail(h, SRJ_EINVAL, "srj_mlp_set_weights: need 6617 values");
     CK(cudaMemcpyAsync(h->mlp_w, w, 6617 * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1070,8 +1090,243 @@ const char *srj_last_error(const srj_handle *h) {
     return h->err.empty() ? "" : h->err.c_str();
 }
 
+srj_status srj_mg_create(const srj_grid *grid, const srj_stencil *stencil,
+                         const srj_mg_opts *opts, void *stream, srj_handle **out) {
+    if (out) *out = nullptr;
+    if (!grid || !out || grid->dim < 1 || grid->dim > 3) return SRJ_EINVAL;
+    if (stencil && (stencil->k || stencil->a_diag)) return SRJ_EUNSUPPORTED;
+    // every axis n = 2^k - 1 with one k: the hierarchy halves all axes down to
+    // a single point
+    int k = -1;
+    for (int a = 0; a < grid->dim; ++a) {
+        const long long n = grid->n[a];
+        if (grid->bc[a] != SRJ_BC_DIRICHLET || n < 1 || n > (1LL << 30) || ((n + 1) & n) != 0 ||
+            grid->h[a] < 0 || !std::isfinite(grid->h[a]))
+            return SRJ_EINVAL;
+        int ka = 0;
+        while ((1LL << ka) < n + 1) ++ka;
+        if (k >= 0 && ka != k) return SRJ_EINVAL;
+        k = ka;
+    }
+    srj_mg_opts o{1, 0, 0, 0};
+    if (opts) o = *opts;
+    if (o.smoother_level < 0 || o.smoother_level > kMaxLevel || o.nu1 < 0 || o.nu2 < 0 ||
+        o.max_cycles < 0)
+        return SRJ_EINVAL;
+    srj_handle *h = new (std::nothrow) srj_handle();
+    if (!h) return SRJ_ENOMEM;
+    MgData *m = new (std::nothrow) MgData();
+    if (!m) {
+        delete h;
+        return SRJ_ENOMEM;
+    }
+    h->mg = m;
+    h->stream = (cudaStream_t)stream;
+    m->nu1 = o.nu1 > 0 ? o.nu1 : 1;
+    m->nu2 = o.nu2 > 0 ? o.nu2 : 1;
+    m->max_cycles = o.max_cycles > 0 ? o.max_cycles : 100;
+    m->omegas.resize(kLevelM[o.smoother_level]);
+    scheme_omegas(o.smoother_level, m->omegas.data(), (int)m->omegas.size());
+    MgGeo g{};
+    g.dim = grid->dim;
+    int n3[3] = {(int)grid->n[0], grid->dim > 1 ? (int)grid->n[1] : 1,
+                 grid->dim > 2 ? (int)grid->n[2] : 1};
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < grid->dim; ++a) {
+        const double hh = grid->h[a] > 0 ? grid->h[a] : 1.0 / (double)(n3[a] + 1);
+        const double e = stencil ? stencil->eps[a] : 0.0;
+        if (e < 0 || !std::isfinite(e)) {
+            srj_destroy(h);
+            return SRJ_EINVAL;
+        }
+        c[a] = (e > 0 ? e : 1.0) / (hh * hh);
+    }
+    m->nlev = k;
+    for (int l = 0; l < k; ++l) {
+        g.nx = n3[0];
+        g.ny = n3[1];
+        g.nz = n3[2];
+        g.cx = c[0];
+        g.cy = c[1];
+        g.cz = c[2];
+        g.diag = 2.0 * (c[0] + c[1] + c[2]);
+        m->geo.push_back(g);
+        for (int a = 0; a < grid->dim; ++a) {
+            n3[a] = (n3[a] - 1) / 2;
+            c[a] *= 0.25;  // twice the spacing
+        }
+    }
+    for (int l = 0; l < k; ++l) {
+        const size_t bytes =
+            sizeof(double) * (size_t)m->geo[l].nx * m->geo[l].ny * m->geo[l].nz;
+        double *p[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (double *&q : p)
+            if (dalloc(&q, bytes) != cudaSuccess) {
+                for (double *r : p) dfree(r);
+                srj_destroy(h);
+                return SRJ_ENOMEM;
+            }
+        m->U0.push_back(p[0]);
+        m->U1.push_back(p[1]);
+        m->F.push_back(p[2]);
+        m->R.push_back(p[3]);
+    }
+    if (dalloc(&m->partials, sizeof(double) * mg_partials_needed()) != cudaSuccess ||
+        dalloc(&m->norm2, sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&m->h_norm2, sizeof(double)) != cudaSuccess) {
+        srj_destroy(h);
+        return SRJ_ENOMEM;
+    }
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        srj_destroy(h);
+        return SRJ_ECUDA;
+    }
+    *out = h;
+    return SRJ_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Record one V-cycle from level l down (stream capture); the iterate of level
+// l is in U0 (cur 0) or U1 (cur 1).  Returns the buffer holding it afterwards.
+int mg_record(MgData &m, int l, int cur, cudaStream_t s, cudaError_t &err) {
+    auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+    };
+    const MgGeo &g = m.geo[l];
+    double *U[2] = {m.U0[l], m.U1[l]};
+    if (l == m.nlev - 1) {  // one point: u = f / D from u = 0
+        ck(mg_sweep_launch(g, U[cur], U[cur ^ 1], m.F[l], 1.0, s));
+        m.launches += 1;
+        return cur ^ 1;
+    }
+    auto smooth = [&](int cycles) {
+        for (int c = 0; c < cycles; ++c)
+            for (double w : m.omegas) {
+                ck(mg_sweep_launch(g, U[cur], U[cur ^ 1], m.F[l], w, s));
+                cur ^= 1;
+                m.launches += 1;
+                if (l == 0) m.fine_sweeps += 1;
+            }
+    };
+    smooth(m.nu1);
+    ck(mg_residual_launch(g, U[cur], m.F[l], m.R[l], nullptr, nullptr, s));
+    ck(mg_restrict_launch(g, m.R[l], m.geo[l + 1], m.F[l + 1], s));
+    const MgGeo &gc = m.geo[l + 1];
+    ck(cudaMemsetAsync(m.U0[l + 1], 0, sizeof(double) * (size_t)gc.nx * gc.ny * gc.nz, s));
+    const int cc = mg_record(m, l + 1, 0, s, err);
+    ck(mg_prolong_launch(gc, cc ? m.U1[l + 1] : m.U0[l + 1], g, U[cur], s));
+    m.launches += 3;
+    smooth(m.nu2);
+    return cur;
+}
+
+// ||f - A u||^2 of the fine level (in U0) into the pinned host word.
+void mg_norm(MgData &m, cudaStream_t s, cudaError_t &err) {
+    int np = 0;
+    cudaError_t e = mg_residual_launch(m.geo[0], m.U0[0], m.F[0], nullptr, m.partials, &np, s);
+    if (e == cudaSuccess) e = mg_sum_launch(m.partials, np, m.norm2, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m.h_norm2, m.norm2, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+}
+
+}  // namespace
+
+extern "C" {
+
+srj_status srj_mg_solve(srj_handle *h, const double *f, double *u, double tol, srj_stats *stats) {
+    if (!h) return SRJ_EINVAL;
+    MgData *m = h->mg;
+    if (!m) return fail(h, SRJ_EINVAL, "srj_mg_solve: not a multigrid handle");
+    if (!f || !u || !(tol > 0) || !std::isfinite(tol))
+        return fail(h, SRJ_EINVAL, "srj_mg_solve: null array or tol not a positive finite number");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    cudaStream_t s = h->stream;
+    const MgGeo &g0 = m->geo[0];
+    const size_t bytes = sizeof(double) * (size_t)g0.nx * g0.ny * g0.nz;
+    if (!m->exec) {  // capture one V-cycle (ending in U0 of the fine level) + its norm
+        // on the handle's private stream (the legacy default stream cannot be
+        // captured); the graph is then launched on the caller's stream
+        cudaError_t err = cudaSuccess;
+        cudaStream_t cs = m->cap;
+        m->launches = 0;
+        m->fine_sweeps = 0;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const int fin = mg_record(*m, 0, 0, cs, err);
+        if (fin != 0) {
+            if (err == cudaSuccess)
+                err = cudaMemcpyAsync(m->U0[0], m->U1[0], bytes, cudaMemcpyDeviceToDevice, cs);
+            m->launches += 1;
+        }
+        mg_norm(*m, cs, err);
+        m->launches += 2;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (err != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(h, SRJ_ECUDA, std::string("srj_mg_solve: capture: ") +
+                                          cudaGetErrorString(err != cudaSuccess ? err : e2));
+        }
+        m->graph = graph;
+        CK(cudaGraphInstantiate(&m->exec, m->graph, 0));
+    }
+    CK(cudaEventRecord(h->ev0, s));
+    CK(cudaMemcpyAsync(m->F[0], f, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(m->U0[0], u, bytes, cudaMemcpyDeviceToDevice, s));
+    cudaError_t err = cudaSuccess;
+    mg_norm(*m, s, err);
+    CK(err);
+    CK(cudaStreamSynchronize(s));
+    const double r0 = std::sqrt(*m->h_norm2);
+    double rn = r0;
+    long long cycles = 0;
+    srj_status result = SRJ_ENOTCONV;
+    if (!std::isfinite(r0)) result = SRJ_EDIVERGED;
+    else if (r0 == 0.0) result = SRJ_OK;
+    while (result == SRJ_ENOTCONV && cycles < m->max_cycles) {
+        CK(cudaGraphLaunch(m->exec, s));
+        CK(cudaStreamSynchronize(s));
+        cycles += 1;
+        rn = std::sqrt(*m->h_norm2);
+        if (!std::isfinite(rn)) result = SRJ_EDIVERGED;
+        else if (rn / r0 < tol) result = SRJ_OK;
+    }
+    CK(cudaMemcpyAsync(u, m->U0[0], bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    if (stats) {
+        stats->status = result;
+        stats->final_level = 0;
+        stats->sweeps = cycles * m->fine_sweeps;
+        stats->cycles = cycles;
+        stats->outer = 0;
+        stats->passes = cycles * m->launches;
+        stats->r0 = r0;
+        stats->rn = rn;
+        stats->seconds = ms * 1e-3;
+    }
+    return result;
+}
+
 srj_status srj_destroy(srj_handle *h) {
     if (!h) return SRJ_EINVAL;
+    if (MgData *m = h->mg) {
+        if (m->exec) cudaGraphExecDestroy(m->exec);
+        if (m->graph) cudaGraphDestroy(m->graph);
+        for (auto *v : {&m->U0, &m->U1, &m->F, &m->R})
+            for (double *p : *v) dfree(p);
+        dfree(m->partials);
+        dfree(m->norm2);
+        if (m->h_norm2) cudaFreeHost(m->h_norm2);
+        if (m->cap) cudaStreamDestroy(m->cap);
+        delete m;
+    }
     if (BatchData *B = h->batch) {
         if (B->exec) cudaGraphExecDestroy(B->exec);
         if (B->graph) cudaGraphDestroy(B->graph);

@@ -134,7 +134,7 @@ __device__ void finalize_problem(const BatchLaunch &b, int p, const PassPlan &pl
                 S.result = DST_DIVERGED;
                 done = true;
             } else {
-                S.carry = in.level - 3 > 0 ? in.level - 3 : 0;
+                S.carry = in.level - kInnerCarry > 0 ? in.level - kInnerCarry : 0;
                 S.phase = BPH_UPDATE;
             }
         }

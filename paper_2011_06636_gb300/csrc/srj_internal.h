@@ -15,6 +15,12 @@
 namespace srj {
 
 constexpr int kMaxLevel = 24;
+// Mixed precision: each inner solve after the first starts this many levels
+// below the level the previous one ended at.  Measured on the 4096^2 Poisson
+// solve: 0 -> 28 680 sweeps, 1 -> 30 470, 3 -> 32 853, 5 -> 31 858 (the
+// correction's residual is dominated by the same smooth modes the previous
+// inner solve was working on, so restarting lower only repeats the climb).
+constexpr int kInnerCarry = 0;
 constexpr int kNumLevels = 25;
 constexpr int kTotalOmegas = 9710;  // sum of M over the 25 levels
 
@@ -238,5 +244,26 @@ cudaError_t vark_faces_launch(const GridGeo &g, const double *k, double *wx,
                               double *wy, double *wz, double *invd,
                               float *wx32, float *wy32, float *wz32,
                               float *invd32, cudaStream_t s);
+
+// Multigrid with SRJ smoothing (kernels_mg.cu): dense x-fastest FP64 arrays,
+// constant coefficients, zero Dirichlet values.
+struct MgGeo {
+    int dim;
+    int nx, ny, nz;
+    double cx, cy, cz;  // eps_a / h_a^2 (0 for axes >= dim)
+    double diag;        // 2 (cx + cy + cz)
+};
+int mg_partials_needed();
+cudaError_t mg_sweep_launch(const MgGeo &g, const double *u, double *uo, const double *f,
+                            double omega, cudaStream_t s);
+// r (may be null) = f - A u; partials (may be null): per-CTA sums of r^2, their
+// count in *nparts
+cudaError_t mg_residual_launch(const MgGeo &g, const double *u, const double *f, double *r,
+                               double *partials, int *nparts, cudaStream_t s);
+cudaError_t mg_sum_launch(const double *partials, int n, double *out, cudaStream_t s);
+cudaError_t mg_restrict_launch(const MgGeo &gf, const double *r, const MgGeo &gc, double *fc,
+                               cudaStream_t s);
+cudaError_t mg_prolong_launch(const MgGeo &gc, const double *ec, const MgGeo &gf, double *u,
+                              cudaStream_t s);
 
 }  // namespace srj

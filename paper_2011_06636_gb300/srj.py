@@ -26,7 +26,8 @@ SRJ_BC_DIRICHLET, SRJ_BC_NEUMANN = range(2)
 EXPORTS = ["srj_version", "srj_level_m", "srj_scheme_omegas", "srj_create", "srj_solve",
            "srj_solve_host", "srj_run_levels", "srj_residual_norm", "srj_get_trace",
            "srj_create_batched", "srj_solve_batched", "srj_mlp_set_weights", "srj_mlp_forward",
-           "srj_mlp_train", "srj_residual_norm_noalloc", "srj_last_error", "srj_destroy"]
+           "srj_mlp_train", "srj_residual_norm_noalloc", "srj_mg_create", "srj_mg_solve",
+           "srj_last_error", "srj_destroy"]
 
 
 class srj_grid(C.Structure):
@@ -44,6 +45,11 @@ class srj_opts(C.Structure):
                 ("level0", C.c_int32), ("fixed_level", C.c_int32), ("max_level", C.c_int32),
                 ("temporal_depth", C.c_int32), ("trace_capacity", C.c_int32),
                 ("max_sweeps", C.c_int64), ("inner_tol", C.c_double)]
+
+
+class srj_mg_opts(C.Structure):
+    _fields_ = [("smoother_level", C.c_int32), ("nu1", C.c_int32), ("nu2", C.c_int32),
+                ("max_cycles", C.c_int32)]
 
 
 class srj_stats(C.Structure):
@@ -108,6 +114,11 @@ def load(build_if_missing: bool = True):
     L.srj_mlp_train.restype = C.c_int
     L.srj_last_error.argtypes = [H]
     L.srj_last_error.restype = C.c_char_p
+    L.srj_mg_create.argtypes = [C.POINTER(srj_grid), C.POINTER(srj_stencil),
+                                C.POINTER(srj_mg_opts), C.c_void_p, C.POINTER(H)]
+    L.srj_mg_create.restype = C.c_int
+    L.srj_mg_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(srj_stats)]
+    L.srj_mg_solve.restype = C.c_int
     L.srj_destroy.argtypes = [H]
     L.srj_destroy.restype = C.c_int
     _lib = L
@@ -294,6 +305,31 @@ def srj_mlp_train(x_ptr, y_ptr, n, order_ptr, steps, batch, lr, theta_ptr, strea
 
 def srj_last_error(h) -> str:
     return load().srj_last_error(h).decode()
+
+
+def srj_mg_create(n, h=None, eps=None, smoother_level=1, nu1=1, nu2=1, max_cycles=0,
+                  stream=None):
+    """Multigrid with SRJ smoothing (FP64).  Returns an opaque handle (int)."""
+    L = load()
+    g = _grid(n, h)
+    st = srj_stencil()
+    for a in range(3):
+        st.eps[a] = float(eps[a]) if (eps is not None and a < len(eps)) else 0.0
+    o = srj_mg_opts(smoother_level, nu1, nu2, max_cycles)
+    hnd = C.c_void_p()
+    rc = L.srj_mg_create(C.byref(g), C.byref(st), C.byref(o), stream, C.byref(hnd))
+    if rc != SRJ_OK:
+        raise SrjError(rc, "srj_mg_create")
+    return hnd.value
+
+
+def srj_mg_solve(h, f_ptr, u_ptr, tol, raise_on_notconv=False):
+    s = srj_stats()
+    rc = load().srj_mg_solve(h, f_ptr, u_ptr, float(tol), C.byref(s))
+    if rc in (SRJ_ENOTCONV, SRJ_EDIVERGED) and not raise_on_notconv:
+        return s.as_dict()
+    _check(h, rc, "srj_mg_solve")
+    return s.as_dict()
 
 
 def srj_destroy(h):

@@ -64,7 +64,8 @@ def test_binding_structs_and_enums_match_header(tmp_path):
     import subprocess
     from paper_2011_06636_gb300 import srj
     structs = {"srj_grid": srj.srj_grid, "srj_stencil": srj.srj_stencil,
-               "srj_opts": srj.srj_opts, "srj_stats": srj.srj_stats}
+               "srj_opts": srj.srj_opts, "srj_stats": srj.srj_stats,
+               "srj_mg_opts": srj.srj_mg_opts}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "srj.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
