@@ -94,24 +94,25 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
             }
             nb[4] = (DIM > 2 && nz_ && z == 0) ? u_zp : u_zm;
             nb[5] = (DIM > 2 && nz_ && z + 1 == g.nz) ? u_zm : u_zp;
-            const C fi = f[i];
+            // f and the face weights are read-only for the whole solve
+            const C fi = __ldg(f + i);
             T t;
             C diag_i = diag_c;
             if constexpr (VARK) {
                 const C *wx = (const C *)a.bufs.wx;
                 const C *wy = (const C *)a.bufs.wy;
                 const C *wz = (const C *)a.bufs.wz;
-                const C invd_i = ((const C *)a.bufs.invd)[i];
+                const C invd_i = __ldg((const C *)a.bufs.invd + i);
                 C wgt[6];
-                wgt[0] = x > 0 ? wx[i - 1] : C(0);
-                wgt[1] = wx[i];
+                wgt[0] = x > 0 ? __ldg(wx + i - 1) : C(0);
+                wgt[1] = __ldg(wx + i);
                 if (DIM > 1) {
-                    wgt[2] = y > 0 ? wy[i - g.pitch] : C(0);
-                    wgt[3] = wy[i];
+                    wgt[2] = y > 0 ? __ldg(wy + i - g.pitch) : C(0);
+                    wgt[3] = __ldg(wy + i);
                 }
                 if (DIM > 2) {
-                    wgt[4] = z > 0 ? wz[i - g.plane] : C(0);
-                    wgt[5] = wz[i];
+                    wgt[4] = z > 0 ? __ldg(wz + i - g.plane) : C(0);
+                    wgt[5] = __ldg(wz + i);
                 }
                 t = P::t_of(nb, wgt, invd_i, fi, u_c);
                 diag_i = C(1) / invd_i;

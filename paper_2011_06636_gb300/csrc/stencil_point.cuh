@@ -29,15 +29,19 @@ struct Elem<PREC_DF> {
     using C = float;
 };
 
+// The source iterate of a pass is never written during that pass (the pass
+// writes the other buffer of the pair), so it is read through the read-only
+// data path: that also tells the compiler the loads cannot alias the stores,
+// so loads of later points can be issued ahead of earlier stores.
 template <int PREC>
 __device__ __forceinline__ typename Elem<PREC>::T load_u(const IterBufs &b, int which,
                                                         long long i) {
     if constexpr (PREC == PREC_DF) {
         const float *hi = (const float *)b.u[which];
         const float *lo = (const float *)b.ulo[which];
-        return df32{hi[i], lo[i]};
+        return df32{__ldg(hi + i), __ldg(lo + i)};
     } else {
-        return ((const typename Elem<PREC>::T *)b.u[which])[i];
+        return __ldg((const typename Elem<PREC>::T *)b.u[which] + i);
     }
 }
 
