@@ -98,6 +98,51 @@ __device__ __forceinline__ df32 df_t2d_iso(df32 w, df32 e, df32 s, df32 n, float
     return df32{r2.hi, lo};
 }
 
+// Variable-coefficient sweep residual in FP32-pair arithmetic:
+//   t = invd (f + sum_q w_q n_q) - u
+// Every product and pair sum keeps its rounding error; the errors are summed
+// plainly into one low part that is never renormalised on the way (the
+// result is left unnormalised as in df_t2d).  11 FP32 operations per
+// neighbour, 11 more for the scaling and the subtraction.
+template <int NQ>
+__device__ __forceinline__ df32 df_t_vark(const df32 *nb, const float *w, float invd, float f,
+                                          df32 u) {
+    float sh = f, sl = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const df32 pq = df_two_prod(nb[q].hi, w[q]);
+        const float pl = __fmaf_rn(nb[q].lo, w[q], pq.lo);
+        const df32 sq = df_two_sum(sh, pq.hi);
+        sh = sq.hi;
+        sl = __fadd_rn(sl, __fadd_rn(sq.lo, pl));
+    }
+    const df32 m = df_two_prod(sh, invd);
+    const float ml = __fmaf_rn(sl, invd, m.lo);
+    const df32 r = df_two_sum(m.hi, -u.hi);
+    return df32{r.hi, __fsub_rn(__fadd_rn(ml, r.lo), u.lo)};
+}
+
+// Constant-coefficient sweep residual on NA axes in FP32-pair arithmetic:
+//   t = sum_a a_a (n_2a + n_2a+1) + g - u,   g = D^-1 f (scaled right-hand side)
+// with the same single unnormalised low part.  19 FP32 operations per axis,
+// 8 for the subtraction.
+template <int NA>
+__device__ __forceinline__ df32 df_t_axes(const df32 *nb, const float *a, float g, df32 u) {
+    float sh = g, sl = 0.f;
+#pragma unroll
+    for (int ax = 0; ax < NA; ++ax) {
+        const df32 s = df_two_sum(nb[2 * ax].hi, nb[2 * ax + 1].hi);
+        const float slo = __fadd_rn(s.lo, __fadd_rn(nb[2 * ax].lo, nb[2 * ax + 1].lo));
+        const df32 p = df_two_prod(s.hi, a[ax]);
+        const float pl = __fmaf_rn(slo, a[ax], p.lo);
+        const df32 q = df_two_sum(sh, p.hi);
+        sh = q.hi;
+        sl = __fadd_rn(sl, __fadd_rn(q.lo, pl));
+    }
+    const df32 r = df_two_sum(sh, -u.hi);
+    return df32{r.hi, __fsub_rn(__fadd_rn(sl, r.lo), u.lo)};
+}
+
 // u + omega t with one renormalisation (about 14 FP32 operations).
 __device__ __forceinline__ df32 df_axpy(df32 u, df32 t, float omega) {
     const df32 d = df_two_prod(t.hi, omega);

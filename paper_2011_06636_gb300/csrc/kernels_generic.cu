@@ -159,7 +159,17 @@ void *entry_for(int prec, int dim, bool vark) {
 
 // ------------------------------------------------------------------ host side
 GenericPlan generic_plan(int prec, const GridGeo &g, bool vark) {
-    GenericPlan p;
+    GenericPlan p{};
+    if (g.dim == 3 && g.neu == 0) {  // plane-streaming 3D pass
+        const Plane3dPlan q = plane3d_plan(prec, g, vark);
+        p.grid = q.grid;
+        p.block = q.block;
+        p.zchunk = q.zchunk;
+        p.kernel = q.kernel;
+        p.smem = q.smem;
+        p.plane3d = 1;
+        return p;
+    }
     if (g.dim == 1) {
         p.block = dim3(kBlock, 1, 1);
         p.zchunk = 1;
@@ -181,18 +191,26 @@ int generic_partials_needed(const GridGeo &g) {
 
 cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a, cudaStream_t s) {
     GenericPlan p = generic_plan(prec, a.geo, vark);
+    if (p.plane3d) {
+        const cudaError_t e = plane3d_prepare(prec, vark);
+        if (e != cudaSuccess) return e;
+    }
     void *args[] = {(void *)&a, (void *)&p.zchunk};
-    return cudaLaunchKernel(p.kernel, p.grid, p.block, args, 0, s);
+    return cudaLaunchKernel(p.kernel, p.grid, p.block, args, p.smem, s);
 }
 
 cudaError_t add_generic_pass_node(int prec, bool vark, const PassLaunch &a, cudaGraph_t body) {
     GenericPlan p = generic_plan(prec, a.geo, vark);
+    if (p.plane3d) {
+        const cudaError_t e = plane3d_prepare(prec, vark);
+        if (e != cudaSuccess) return e;
+    }
     void *args[] = {(void *)&a, (void *)&p.zchunk};
     cudaKernelNodeParams kp{};
     kp.func = p.kernel;
     kp.gridDim = p.grid;
     kp.blockDim = p.block;
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = p.smem;
     kp.kernelParams = args;
     cudaGraphNode_t node;
     return cudaGraphAddKernelNode(&node, body, nullptr, 0, &kp);

@@ -144,7 +144,19 @@ struct GenericPlan {
     dim3 grid, block;
     int zchunk;
     void *kernel;  // __global__ entry for graph nodes
+    int smem;      // dynamic shared memory bytes
+    int plane3d;   // 1: the 3D plane-streaming kernel (kernels_plane3d.cu)
 };
+// 3D Dirichlet passes: plane-streaming kernel with a cp.async ring of z planes
+// (kernels_plane3d.cu); same grid and partial count as the generic 3D pass.
+struct Plane3dPlan {
+    dim3 grid, block;
+    int zchunk;
+    void *kernel;
+    int smem;
+};
+Plane3dPlan plane3d_plan(int prec, const GridGeo &g, bool vark);
+cudaError_t plane3d_prepare(int prec, bool vark);
 GenericPlan generic_plan(int prec, const GridGeo &g, bool vark);
 int generic_partials_needed(const GridGeo &g);
 cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a,

@@ -78,18 +78,7 @@ struct Point {
     __device__ __forceinline__ static T t_of(const T *nb, const C *wgt, C invd, C f,
                                              T uc) {
         if constexpr (PREC == PREC_DF) {
-            df32 s = df_mul_f(nb[0], wgt[0]);
-            s = df_add(s, df_mul_f(nb[1], wgt[1]));
-            if (DIM > 1) {
-                s = df_add(s, df_mul_f(nb[2], wgt[2]));
-                s = df_add(s, df_mul_f(nb[3], wgt[3]));
-            }
-            if (DIM > 2) {
-                s = df_add(s, df_mul_f(nb[4], wgt[4]));
-                s = df_add(s, df_mul_f(nb[5], wgt[5]));
-            }
-            s = df_add_f(s, f);
-            return df_sub(df_mul_f(s, invd), uc);
+            return df_t_vark<2 * DIM>(nb, wgt, invd, f, uc);
         } else {
             T s = f + wgt[0] * nb[0] + wgt[1] * nb[1];
             if (DIM > 1) s += wgt[2] * nb[2] + wgt[3] * nb[3];
@@ -108,11 +97,7 @@ struct Point {
             if constexpr (DIM == 2) {
                 return df_t2d(nb[0], nb[1], nb[2], nb[3], a[0], a[1], f, uc);
             } else {
-                df32 s = df_mul_f(df_add(nb[0], nb[1]), a[0]);
-                if (DIM > 1) s = df_add(s, df_mul_f(df_add(nb[2], nb[3]), a[1]));
-                if (DIM > 2) s = df_add(s, df_mul_f(df_add(nb[4], nb[5]), a[2]));
-                s = df_add_f(s, f);
-                return df_sub(s, uc);
+                return df_t_axes<DIM>(nb, a, f, uc);
             }
         } else {
             T s = a[0] * (nb[0] + nb[1]);

@@ -82,6 +82,10 @@ CASES = [
     ("3d_20x18x16", [20, 18, 16], None, None),
     ("3d_17x9x12_vark", [17, 9, 12], [1.0, 0.5, 2.0], "vark"),
     ("2d_40x31_vark", [40, 31], None, "vark"),
+    # several 32 x 8 column tiles and z chunks of the 3D plane-streaming pass,
+    # ragged in every direction
+    ("3d_70x19x75", [70, 19, 75], None, None),
+    ("3d_45x33x70_vark", [45, 33, 70], [1.0, 0.7, 1.3], "vark"),
 ]
 
 
