@@ -34,25 +34,6 @@ __device__ __forceinline__ df32 df_two_prod(float a, float b) {
     return {p, e};
 }
 
-__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
-    const df32 s = df_two_sum(a.hi, b.hi);
-    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-
-__device__ __forceinline__ df32 df_sub(df32 a, df32 b) {
-    return df_add(a, df32{-b.hi, -b.lo});
-}
-
-__device__ __forceinline__ df32 df_add_f(df32 a, float b) {
-    const df32 s = df_two_sum(a.hi, b);
-    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
-}
-
-__device__ __forceinline__ df32 df_mul_f(df32 a, float b) {
-    const df32 p = df_two_prod(a.hi, b);
-    return df_fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
-}
-
 __device__ __forceinline__ double df_to_double(df32 a) {
     return (double)a.hi + (double)a.lo;
 }
