@@ -64,6 +64,7 @@ struct srj_handle {
     // graph of the device-driven cycle loop
     bool host_loop = false;  // SRJ_LAUNCH=host: passes launched by a host loop
     bool use_wave = false;   // 2D constant coefficients: temporally blocked passes
+    int small_smem = 0;      // > 0: the grid fits one CTA's shared memory (kernels_small.cu)
     Wave2dPlan wplan{};
     int num_sms = 0;
     cudaGraph_t graph = nullptr;
@@ -208,6 +209,11 @@ srj_status build_graph(srj_handle *h) {
 // graphs) the same pass kernel is launched directly in batches of 64 and the
 // state is polled after each batch; passes issued after the end exit at once.
 srj_status run_loop(srj_handle *h) {
+    if (h->small_smem > 0 && !h->host_loop) {  // the whole solve in one CTA
+        PassLaunch a = make_launch(h, true);
+        CK(small_solve_launch(h->kprec, h->vark, a, h->stream));
+        return SRJ_OK;
+    }
     if (!h->host_loop) {
         CK(cudaGraphLaunch(h->exec, h->stream));
         return SRJ_OK;
@@ -744,6 +750,7 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
         const char *lm = std::getenv("SRJ_LAUNCH");
         h->host_loop = lm && std::strcmp(lm, "host") == 0;
     }
+    h->small_smem = small_solve_smem(h->kprec, h->vark, g);
     h->partials_cap = generic_partials_needed(g);
     if (h->use_wave) {
         h->wplan = wave2d_plan(h->kprec, wave2d_depth(h->kprec, o.temporal_depth), g, h->num_sms);

@@ -164,6 +164,11 @@ cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a,
 cudaError_t add_generic_pass_node(int prec, bool vark, const PassLaunch &a,
                                   cudaGraph_t body);
 
+// Whole solve of a small grid in one CTA (kernels_small.cu): the dynamic
+// shared memory it needs, 0 when the grid does not fit.
+int small_solve_smem(int prec, bool vark, const GridGeo &g);
+cudaError_t small_solve_launch(int prec, bool vark, const PassLaunch &a, cudaStream_t s);
+
 // Temporally blocked 2D constant-coefficient pass (kernels_wave2d.cu).
 struct Wave2dPlan {
     int T;        // sweeps fused per pass

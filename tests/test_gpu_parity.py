@@ -435,3 +435,41 @@ def test_non_finite_input_reports_diverged(S, n, prec):
         S.srj_destroy(h)
     assert st["status"] == S.SRJ_EDIVERGED
     assert st["sweeps"] == 0
+
+
+@pytest.mark.parametrize("n,prec,kind", [([1024], "F64", None), ([64, 48], "F64", None),
+                                         ([20, 18, 16], "F64", None), ([17, 9, 12], "F64", "vark"),
+                                         ([40, 31], "MIXED", "vark"), ([77, 50], "MIXED", None)])
+def test_one_cta_solve_matches_pass_kernels(S, orc, n, prec, kind, monkeypatch):
+    # small grids run the whole solve in one CTA; SRJ_LAUNCH=host forces the
+    # per-pass kernels: same levels, same sweeps, same solution
+    p = {"F64": S.SRJ_PREC_F64, "MIXED": S.SRJ_PREC_MIXED}[prec]
+    dt = torch.float64
+    f = inputs.uniform_rhs(n, seed=9).ravel()
+    k = inputs.lognormal_k(n, seed=3, corr=4.0) if kind else None
+    tol = 1e-8
+    out = {}
+    for mode in ("one_cta", "passes"):
+        if mode == "passes":
+            monkeypatch.setenv("SRJ_LAUNCH", "host")
+        h, kt = make(S, n, p, k=k, trace_capacity=10000)
+        try:
+            fd = dev(f, dt)
+            ud = torch.zeros_like(fd)
+            st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), tol)
+            lv, _ = S.srj_get_trace(h)
+        finally:
+            S.srj_destroy(h)
+        out[mode] = (st, lv, ud.cpu().double().numpy())
+        monkeypatch.delenv("SRJ_LAUNCH", raising=False)
+    (s1, l1, u1), (s2, l2, u2) = out["one_cta"], out["passes"]
+    assert s1["status"] == S.SRJ_OK and s2["status"] == S.SRJ_OK
+    scale = np.abs(u2).max()
+    if prec == "F64":
+        np.testing.assert_array_equal(l1, l2)
+        assert s1["sweeps"] == s2["sweeps"]
+        np.testing.assert_allclose(u1, u2, rtol=0, atol=1e-12 * scale)
+    else:
+        # the inner FP32-pair sweeps round differently in the two kernels;
+        # both solutions meet the same FP64 residual tolerance
+        np.testing.assert_allclose(u1, u2, rtol=0, atol=1e-6 * scale)
