@@ -65,6 +65,7 @@ struct srj_handle {
     bool host_loop = false;  // SRJ_LAUNCH=host: passes launched by a host loop
     bool use_wave = false;   // 2D constant coefficients: temporally blocked passes
     int small_smem = 0;      // > 0: the grid fits one CTA's shared memory (kernels_small.cu)
+    Plane3dMaps *p3maps = nullptr;  // TMA tensor maps of the 3D pass (host copy)
     Wave2dPlan wplan{};
     int num_sms = 0;
     cudaGraph_t graph = nullptr;
@@ -197,7 +198,7 @@ srj_status build_graph(srj_handle *h) {
         CK(wave2d_prepare(h->kprec, h->wplan.T));
         CK(add_wave2d_node(h->wplan, a, body));
     } else {
-        CK(add_generic_pass_node(h->kprec, h->vark, a, body));
+        CK(add_generic_pass_node(h->kprec, h->vark, a, body, h->p3maps));
     }
     CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
     return SRJ_OK;
@@ -222,7 +223,7 @@ srj_status run_loop(srj_handle *h) {
     for (;;) {
         for (int i = 0; i < 64; ++i) {
             if (h->use_wave) CK(wave2d_launch(h->wplan, a, h->stream));
-            else CK(generic_pass_launch(h->kprec, h->vark, a, h->stream));
+            else CK(generic_pass_launch(h->kprec, h->vark, a, h->stream, h->p3maps));
         }
         DevState *probe = h->h_st;
         CK(cudaMemcpyAsync(probe, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
@@ -256,6 +257,8 @@ srj_status status_of(int dst) {
             return SRJ_OK;
         case DST_DIVERGED:
             return SRJ_EDIVERGED;
+        case DST_TIMEOUT:
+            return SRJ_ETIMEOUT;
         default:
             return SRJ_ENOTCONV;
     }
@@ -299,7 +302,7 @@ srj_status solve_plain(srj_handle *h, const void *f, void *u, double tol, int se
         h->h_st->cur = fin.cur;
         CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
         PassLaunch a = make_launch(h, false);
-        CK(generic_pass_launch(h->kprec, h->vark, a, st));
+        CK(generic_pass_launch(h->kprec, h->vark, a, st, h->p3maps));
         CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         stats->rn = h->h_st->r0;
@@ -807,6 +810,15 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
                "face weights");
         }
     }
+    if (g.dim == 3 && g.neu == 0 && rc == SRJ_OK) {  // the 3D pass stages planes by TMA
+        h->p3maps = new (std::nothrow) Plane3dMaps();
+        if (!h->p3maps) {
+            srj_destroy(h);
+            return SRJ_ENOMEM;
+        }
+        const PassLaunch a = make_launch(h, false);
+        ck(plane3d_encode(h->kprec, h->vark, g, a.bufs, h->p3maps), "tensor maps");
+    }
     ck(cudaEventCreate(&h->ev0), "event");
     ck(cudaEventCreate(&h->ev1), "event");
     ck(cudaStreamSynchronize(s), "create sync");
@@ -916,7 +928,7 @@ srj_status srj_residual_norm(srj_handle *h, const void *f, const void *u, double
     init_state(h, *h->h_st, 1.0, SRJ_TOL_REL, DSEL_HEURISTIC, 0, 0, 0, 0, 0);
     CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
     PassLaunch a = make_launch(h, false);
-    CK(generic_pass_launch(h->kprec, h->vark, a, st));
+    CK(generic_pass_launch(h->kprec, h->vark, a, st, h->p3maps));
     CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     *out = h->h_st->r0;
@@ -1356,6 +1368,7 @@ srj_status srj_destroy(srj_handle *h) {
         dfree(p);
     if (h->h_st) cudaFreeHost(h->h_st);
     if (h->h_onorm2) cudaFreeHost(h->h_onorm2);
+    delete h->p3maps;
     delete h;
     return SRJ_OK;
 }

@@ -189,23 +189,27 @@ int generic_partials_needed(const GridGeo &g) {
     return (int)(p.grid.x * p.grid.y * p.grid.z);
 }
 
-cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a, cudaStream_t s) {
+cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a, cudaStream_t s,
+                                const Plane3dMaps *maps) {
     GenericPlan p = generic_plan(prec, a.geo, vark);
     if (p.plane3d) {
+        if (!maps) return cudaErrorInvalidValue;
         const cudaError_t e = plane3d_prepare(prec, vark);
         if (e != cudaSuccess) return e;
     }
-    void *args[] = {(void *)&a, (void *)&p.zchunk};
+    void *args[] = {(void *)&a, (void *)&p.zchunk, (void *)maps};
     return cudaLaunchKernel(p.kernel, p.grid, p.block, args, p.smem, s);
 }
 
-cudaError_t add_generic_pass_node(int prec, bool vark, const PassLaunch &a, cudaGraph_t body) {
+cudaError_t add_generic_pass_node(int prec, bool vark, const PassLaunch &a, cudaGraph_t body,
+                                  const Plane3dMaps *maps) {
     GenericPlan p = generic_plan(prec, a.geo, vark);
     if (p.plane3d) {
+        if (!maps) return cudaErrorInvalidValue;
         const cudaError_t e = plane3d_prepare(prec, vark);
         if (e != cudaSuccess) return e;
     }
-    void *args[] = {(void *)&a, (void *)&p.zchunk};
+    void *args[] = {(void *)&a, (void *)&p.zchunk, (void *)maps};
     cudaKernelNodeParams kp{};
     kp.func = p.kernel;
     kp.gridDim = p.grid;

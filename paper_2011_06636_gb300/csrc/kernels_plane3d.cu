@@ -1,14 +1,20 @@
 // kernels_plane3d.cu -- the 3D SRJ pass (one relaxed sweep or one residual per
 // pass, Sec. 2 Eq. relaxed-jacobi and Sec. 3 Eq. relative-residual) as a
 // plane-streaming kernel: a CTA owns a 32 x 8 column tile and walks a chunk of
-// z planes; every plane it needs (the iterate with a one-cell halo, the
-// right-hand side and, for variable coefficients, the face weights and 1/D)
-// is staged into a shared-memory ring by cp.async several planes ahead, so the
-// loads of plane z + 3 are in flight while plane z is computed.  Points outside
-// the grid are zero-filled by the copies (zero Dirichlet values, zero faces).
-// Same pass protocol as the generic kernel: plan_pass / finish_pass.
+// z planes.  Every plane it needs -- the iterate with a one-cell halo, the
+// right-hand side and, for variable coefficients, the face weights and 1/D --
+// is brought into a five-slot shared-memory ring by TMA tensor copies
+// (cp.async.bulk.tensor, one elected thread, one mbarrier per slot), three
+// planes ahead of the plane computed.  The tensor maps bound every array to
+// the grid, so the copies zero-fill the ghost rows, columns and planes: the
+// zero Dirichlet values and zero boundary faces.  Same pass protocol as the
+// generic kernel: plan_pass / finish_pass.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
+
+#include <cstring>
 
 #include "df32.cuh"
 #include "pass_common.cuh"
@@ -18,66 +24,95 @@
 namespace srj {
 namespace {
 
-constexpr int kTX = 32, kTY = 8;  // column tile
-constexpr int kHX = 4;            // columns staged left of the tile (16-byte aligned rows)
+constexpr int kTX = 32, kTY = 8;    // column tile (threads)
+constexpr int kHX = 4;              // columns staged left of the tile: x0 - 4 is 16-byte aligned
 constexpr int kSX = kTX + 2 * kHX;  // staged row width: x0 - 4 .. x0 + 35
-constexpr int kPD = 3;            // planes issued ahead of the one computed
-constexpr int kNS = kPD + 2;      // ring slots: planes z-1 .. z+PD
+constexpr int kPD = 3;              // planes in flight ahead of the one computed
+constexpr int kNS = kPD + 2;        // ring slots: planes z-1 .. z+PD
+constexpr long long kWaitLimit = 1LL << 22;  // bounded mbarrier wait (iterations)
 
-// Shared-memory layout of one ring slot.  Every staged row starts on a
-// 16-byte boundary in global and shared memory so that it moves in 16-byte
-// cp.async chunks: the iterate rows y0-1 .. y0+8 and x faces rows y0 .. y0+7
-// cover columns x0-4 .. x0+35 (the halo columns x0-1 and x0+32 inside);
-// the right-hand side, z faces and 1/D cover the tile; y faces rows
-// y0-1 .. y0+7.  ES is the element size (4 or 8 bytes).
+__host__ __device__ constexpr int al128(int b) { return (b + 127) / 128 * 128; }
+
+// One ring slot: every array at a 128-byte aligned offset.  Boxes (elements):
+// iterate {40, 10} from (x0-4, y0-1); x faces {40, 8} from (x0-4, y0);
+// y faces {32, 9} from (x0, y0-1); rhs, z faces, 1/D {32, 8} from (x0, y0).
 template <int PREC, bool VARK>
 struct Plane {
     static constexpr bool LO = PREC == PREC_DF;
     static constexpr int ES = PREC == PREC_F64 ? 8 : 4;
-    static constexpr int U = kSX * (kTY + 2);       // iterate (hi), rows y0-1 .. y0+8
-    static constexpr int F = kTX * kTY;
-    static constexpr int WX = VARK ? kSX * kTY : 0;
-    static constexpr int WY = VARK ? kTX * (kTY + 1) : 0;
-    static constexpr int WZ = VARK ? kTX * kTY : 0;
-    static constexpr int ID = VARK ? kTX * kTY : 0;
-    static constexpr int o_lo = U, o_f = U * (LO ? 2 : 1), o_wx = o_f + F, o_wy = o_wx + WX,
-                         o_wz = o_wy + WY, o_id = o_wz + WZ;
-    static constexpr int ELEMS = o_id + ID;
-    static constexpr int BYTES = ((ELEMS * ES + 15) / 16) * 16;
+    static constexpr int BU = kSX * (kTY + 2) * ES, BF = kTX * kTY * ES;
+    static constexpr int BWX = kSX * kTY * ES, BWY = kTX * (kTY + 1) * ES;
+    static constexpr int o_hi = 0, o_lo = o_hi + al128(BU), o_f = o_lo + (LO ? al128(BU) : 0);
+    static constexpr int o_wx = o_f + al128(BF), o_wy = o_wx + (VARK ? al128(BWX) : 0);
+    static constexpr int o_wz = o_wy + (VARK ? al128(BWY) : 0), o_id = o_wz + (VARK ? al128(BF) : 0);
+    static constexpr int BYTES = o_id + (VARK ? al128(BF) : 0);
     static constexpr int SMEM = kNS * BYTES;
-    static constexpr int EPC = 16 / ES;  // elements per 16-byte chunk
+    // bytes one plane's copies deliver (the transaction count of its barrier)
+    static constexpr unsigned TX = BU * (LO ? 2 : 1) + BF + (VARK ? BWX + BWY + 2 * BF : 0);
 };
 
-__device__ __forceinline__ void cp16(void *smem, const void *g, bool ok, const void *safe) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const void *src = ok ? g : safe;
-    const int n = ok ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(n));
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cpa_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+__device__ __forceinline__ void bar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// true once the phase with the given parity has completed; false after the
+// iteration limit
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma3(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                     uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
 }
 
 template <int PREC, bool VARK>
-__global__ void __launch_bounds__(kTX * kTY) plane3d_kernel(PassLaunch a, int zchunk) {
+__global__ void __launch_bounds__(kTX * kTY)
+    plane3d_kernel(PassLaunch a, int zchunk, const __grid_constant__ Plane3dMaps maps) {
     using T = typename Elem<PREC>::T;
     using C = typename Elem<PREC>::C;
     using P = Point<PREC, 3>;
     using L = Plane<PREC, VARK>;
     constexpr int ES = L::ES;
-    extern __shared__ __align__(16) unsigned char smem[];
-
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_bar[kNS];
     __shared__ PassPlan s_plan;
     __shared__ double s_omega;
+    __shared__ int s_err;
+
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kTX * ty;
     if (tid == 0) {
         s_plan = plan_pass(a, 1);
         s_omega = (s_plan.run && s_plan.nsw) ? a.w64[s_plan.woff] : 0.0;
+        s_err = 0;
         if (!s_plan.run && a.cfg.use_cond && blockIdx.x == 0 && blockIdx.y == 0 &&
             blockIdx.z == 0)
             cudaGraphSetConditional(a.cfg.cond, 0);
+        if (s_plan.run) {
+            for (int k = 0; k < kNS; ++k) bar_init(&s_bar[k]);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
     }
     __syncthreads();
     const PassPlan p = s_plan;
@@ -89,61 +124,41 @@ __global__ void __launch_bounds__(kTX * kTY) plane3d_kernel(PassLaunch a, int zc
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
     const int src = p.cur, dst = p.cur ^ 1;
-    const unsigned char *uhi = (const unsigned char *)a.bufs.u[src];
-    const unsigned char *ulo = (const unsigned char *)a.bufs.ulo[src];
-    const unsigned char *fb = (const unsigned char *)a.bufs.f;
-    const unsigned char *wxb = (const unsigned char *)a.bufs.wx;
-    const unsigned char *wyb = (const unsigned char *)a.bufs.wy;
-    const unsigned char *wzb = (const unsigned char *)a.bufs.wz;
-    const unsigned char *idb = (const unsigned char *)a.bufs.invd;
     const bool dinf = a.dinf && p.nsw;
 
-    // Copy plane zz into ring slot zz mod NS in 16-byte chunks.  A chunk is
-    // copied when it lies inside the grid's rows and planes and inside the
-    // padded row [0, pitch) (pitch is a multiple of 32, so a chunk is either
-    // wholly inside or wholly outside); otherwise it is zero-filled: the
-    // zero Dirichlet values of the ghost rows, columns and planes, and zero
-    // faces there.  Columns in [nx, pitch) are zero in memory.
-    auto issue = [&](int zz) {
-        unsigned char *slot = smem + ((zz + kNS) % kNS) * L::BYTES;
-        const bool zok = zz >= 0 && zz < g.nz;
-        const long long pz = (long long)g.plane * (zok ? zz : 0);
-        // one array segment: rows [r0, r0 + nr) of the tile, columns
-        // [c0, c0 + cw), into smem at element offset so (row stride cw)
-        auto seg = [&](const unsigned char *base, int so, int r0, int nr, int c0, int cw) {
-            const int cpr = cw / L::EPC;
-            for (int q = tid; q < nr * cpr; q += kTX * kTY) {
-                const int rr = q / cpr, cc = q - rr * cpr;
-                const int gy = y0 + r0 + rr, gx = x0 + c0 + cc * L::EPC;
-                const bool ok = zok && gy >= 0 && gy < g.ny && gx >= 0 && gx < g.pitch;
-                const long long off = (pz + (long long)g.pitch * (ok ? gy : 0) + (ok ? gx : 0)) * ES;
-                cp16(slot + (so + rr * cw + cc * L::EPC) * ES, base + off, ok, base);
-            }
-        };
-        seg(uhi, 0, -1, kTY + 2, -kHX, kSX);
-        if constexpr (L::LO) seg(ulo, L::o_lo, -1, kTY + 2, -kHX, kSX);
-        seg(fb, L::o_f, 0, kTY, 0, kTX);
+    // plane zz (>= z0 - 1) lives in slot (zz - z0 + 1) mod NS; the n-th plane
+    // of a slot completes its barrier's phase n, parity n & 1
+    auto rel = [&](int zz) { return zz - (z0 - 1); };
+    auto slot = [&](int zz) -> unsigned char * { return smem + (rel(zz) % kNS) * L::BYTES; };
+    auto issue = [&](int zz) {  // one thread
+        unsigned char *s = slot(zz);
+        uint64_t *bar = &s_bar[rel(zz) % kNS];
+        // order the block's earlier reads of this slot before the async writes
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        bar_expect(bar, L::TX);
+        tma3(s + L::o_hi, &maps.u[src], x0 - kHX, y0 - 1, zz, bar);
+        if constexpr (L::LO) tma3(s + L::o_lo, &maps.ulo[src], x0 - kHX, y0 - 1, zz, bar);
+        tma3(s + L::o_f, &maps.f, x0, y0, zz, bar);
         if constexpr (VARK) {
-            seg(wxb, L::o_wx, 0, kTY, -kHX, kSX);
-            seg(wyb, L::o_wy, -1, kTY + 1, 0, kTX);
-            seg(wzb, L::o_wz, 0, kTY, 0, kTX);
-            seg(idb, L::o_id, 0, kTY, 0, kTX);
+            tma3(s + L::o_wx, &maps.wx, x0 - kHX, y0, zz, bar);
+            tma3(s + L::o_wy, &maps.wy, x0, y0 - 1, zz, bar);
+            tma3(s + L::o_wz, &maps.wz, x0, y0, zz, bar);
+            tma3(s + L::o_id, &maps.invd, x0, y0, zz, bar);
         }
-        cpa_commit();
     };
-    auto sl = [&](int zz) -> const unsigned char * {
-        return smem + ((zz + kNS) % kNS) * L::BYTES;
+    auto wait = [&](int zz) -> bool {
+        return bar_wait(&s_bar[rel(zz) % kNS], (unsigned)((rel(zz) / kNS) & 1));
     };
-    auto ld = [&](const unsigned char *slot, int idx) -> C {
-        return *(const C *)(slot + idx * ES);
+    auto ld = [&](const unsigned char *s, int off, int idx) -> C {
+        return *(const C *)(s + off + idx * ES);
     };
     // iterate at tile column cx (-1 .. 32) and row cy (-1 .. 8)
-    auto ldu = [&](const unsigned char *slot, int cx, int cy) -> T {
+    auto ldu = [&](const unsigned char *s, int cx, int cy) -> T {
         const int c = (cx + kHX) + kSX * (cy + 1);
         if constexpr (L::LO)
-            return df32{*(const float *)(slot + c * ES), *(const float *)(slot + (L::o_lo + c) * ES)};
+            return df32{*(const float *)(s + L::o_hi + c * 4), *(const float *)(s + L::o_lo + c * 4)};
         else
-            return *(const T *)(slot + c * ES);
+            return *(const T *)(s + L::o_hi + c * ES);
     };
 
     C cconst[3], invd_c = C(1.0 / g.diag), diag_c = C(g.diag);
@@ -151,19 +166,27 @@ __global__ void __launch_bounds__(kTX * kTY) plane3d_kernel(PassLaunch a, int zc
     cconst[1] = C(g.cy / g.diag);
     cconst[2] = C(g.cz / g.diag);
 
-    // prologue: planes z0 - 1 .. z0 + PD - 1
-    for (int zz = z0 - 1; zz < z0 + kPD; ++zz) issue(zz);
+    if (tid == 0)
+        for (int zz = z0 - 1; zz < z0 + kPD; ++zz) issue(zz);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool active = gx < g.nx && gy < g.ny;
     const long long col = (long long)gx + g.pitch * gy;
     double part = 0.0;
+    int last_issued = z0 + kPD - 1;  // planes issued so far: z0 - 1 .. last_issued
+    int next_wait = z0 - 1;          // first plane not yet waited for
+    bool ok = true;
     for (int z = z0; z < z1; ++z) {
-        // issued so far: planes up to z + PD - 1, one group each; all but the
-        // newest PD - 2 are complete, so planes z - 1, z, z + 1 have landed
-        cpa_wait<kPD - 2>();
-        __syncthreads();      // everyone's did; everyone finished plane z - 1
-        issue(z + kPD);       // into the slot of plane z - 2
-        const unsigned char *sm = sl(z - 1), *s0 = sl(z), *sp = sl(z + 1);
+        for (; next_wait <= z + 1; ++next_wait) ok = ok && wait(next_wait);
+        // one decision for the whole block (a bounded wait may run out in one
+        // thread and not in another); the barrier also means every thread is
+        // done with plane z - 2's slot
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) issue(z + kPD);
+        last_issued = z + kPD;
+        const unsigned char *sm = slot(z - 1), *s0 = slot(z), *sp = slot(z + 1);
         if (active) {
             T nb[6];
             nb[0] = ldu(s0, tx - 1, ty);
@@ -173,18 +196,18 @@ __global__ void __launch_bounds__(kTX * kTY) plane3d_kernel(PassLaunch a, int zc
             nb[4] = ldu(sm, tx, ty);
             nb[5] = ldu(sp, tx, ty);
             const T u_c = ldu(s0, tx, ty);
-            const C fi = ld(s0, L::o_f + tid);
+            const C fi = ld(s0, L::o_f, tid);
             T t;
             C diag_i = diag_c;
             if constexpr (VARK) {
                 C wgt[6];
-                wgt[0] = ld(s0, L::o_wx + ty * kSX + kHX + tx - 1);
-                wgt[1] = ld(s0, L::o_wx + ty * kSX + kHX + tx);
-                wgt[2] = ld(s0, L::o_wy + ty * kTX + tx);
-                wgt[3] = ld(s0, L::o_wy + (ty + 1) * kTX + tx);
-                wgt[4] = ld(sm, L::o_wz + tid);
-                wgt[5] = ld(s0, L::o_wz + tid);
-                const C invd_i = ld(s0, L::o_id + tid);
+                wgt[0] = ld(s0, L::o_wx, ty * kSX + kHX + tx - 1);
+                wgt[1] = ld(s0, L::o_wx, ty * kSX + kHX + tx);
+                wgt[2] = ld(s0, L::o_wy, ty * kTX + tx);
+                wgt[3] = ld(s0, L::o_wy, (ty + 1) * kTX + tx);
+                wgt[4] = ld(sm, L::o_wz, tid);
+                wgt[5] = ld(s0, L::o_wz, tid);
+                const C invd_i = ld(s0, L::o_id, tid);
                 t = P::t_of(nb, wgt, invd_i, fi, u_c);
                 diag_i = C(1) / invd_i;
             } else {
@@ -201,7 +224,12 @@ __global__ void __launch_bounds__(kTX * kTY) plane3d_kernel(PassLaunch a, int zc
             }
         }
     }
-    cpa_wait<0>();
+    // copies still in flight land before the CTA's shared memory goes away
+    // (each wait is bounded); a wait that ran out marks the solve
+    for (; next_wait <= last_issued; ++next_wait) ok = wait(next_wait) && ok;
+    if (!ok) atomicOr(&s_err, 1);
+    __syncthreads();
+    if (s_err && tid == 0) atomicExch(&a.st->status, (int)DST_TIMEOUT);
     double tot = 0.0;
     if (p.resid) tot = block_sum(part);
     else if (dinf) tot = block_max(part);
@@ -223,6 +251,11 @@ cudaError_t plane_prepare() {
     if (e == cudaSuccess) done = true;
     return e;
 }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 }  // namespace
 
@@ -250,6 +283,54 @@ cudaError_t plane3d_prepare(int prec, bool vark) {
     if (prec == PREC_F64) return vark ? plane_prepare<PREC_F64, true>() : plane_prepare<PREC_F64, false>();
     if (prec == PREC_F32) return vark ? plane_prepare<PREC_F32, true>() : plane_prepare<PREC_F32, false>();
     return vark ? plane_prepare<PREC_DF, true>() : plane_prepare<PREC_DF, false>();
+}
+
+// Tensor maps of the staged arrays: 3D {nx, ny, nz} over the padded layout
+// (row stride pitch, plane stride pitch * ny elements), boxes as in Plane.
+// Coordinates outside {nx, ny, nz} read as zero.
+cudaError_t plane3d_encode(int prec, bool vark, const GridGeo &g, const IterBufs &b,
+                           Plane3dMaps *m) {
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                               cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = (EncodeTiledFn)fn;
+    }
+    const int es = prec == PREC_F64 ? 8 : 4;
+    const CUtensorMapDataType dt =
+        prec == PREC_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.plane * es};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    auto enc = [&](CUtensorMap *map, const void *base, cuuint32_t bx, cuuint32_t by) -> cudaError_t {
+        const cuuint32_t box[3] = {bx, by, 1};
+        const CUresult r = encode(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    };
+    std::memset((void *)m, 0, sizeof(*m));
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t x) {
+        if (x != cudaSuccess && e == cudaSuccess) e = x;
+    };
+    for (int k = 0; k < 2; ++k) {
+        ck(enc(&m->u[k], b.u[k], kSX, kTY + 2));
+        if (prec == PREC_DF) ck(enc(&m->ulo[k], b.ulo[k], kSX, kTY + 2));
+    }
+    ck(enc(&m->f, b.f, kTX, kTY));
+    if (vark) {
+        ck(enc(&m->wx, b.wx, kSX, kTY));
+        ck(enc(&m->wy, b.wy, kTX, kTY + 1));
+        ck(enc(&m->wz, b.wz, kTX, kTY));
+        ck(enc(&m->invd, b.invd, kTX, kTY));
+    }
+    return e;
 }
 
 }  // namespace srj

@@ -90,6 +90,7 @@ __device__ __forceinline__ float hist_log(double ratio) {
 __device__ void advance_state(DevState *st, const SolveCfg &cfg, const PassPlan &p,
                               double norm2, int mlp_pick = -1, double dmax = -1.0) {
     st->passes += 1;
+    if (st->status != DST_RUNNING) return;  // a CTA of this pass recorded a failure
     if (p.nsw > 0) {
         st->cur ^= 1;
         st->k += p.nsw;

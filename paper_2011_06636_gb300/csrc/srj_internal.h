@@ -7,6 +7,7 @@
 //   interior are zero (Dirichlet).  1D grids use ny = nz = 1, 2D nz = 1.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (types only; the encoder is looked up at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -48,7 +49,8 @@ enum DevStatus : int32_t {
     DST_NOTCONV = 2,
     DST_DIVERGED = 3,
     DST_STALLED = 4,  // inner solve of mixed precision: a cycle raised the residual
-    DST_DONE = 5      // explicit schedule finished
+    DST_DONE = 5,     // explicit schedule finished
+    DST_TIMEOUT = 6   // a bounded device-side wait ran out (SRJ_ETIMEOUT)
 };
 
 // Per-solve state in device memory.  The host writes the whole struct (the
@@ -157,12 +159,21 @@ struct Plane3dPlan {
 };
 Plane3dPlan plane3d_plan(int prec, const GridGeo &g, bool vark);
 cudaError_t plane3d_prepare(int prec, bool vark);
+// TMA tensor maps of the arrays the 3D pass stages (iterate pair hi / lo,
+// rhs, face weights, 1/D), encoded once per handle.
+struct Plane3dMaps {
+    CUtensorMap u[2], ulo[2], f, wx, wy, wz, invd;
+};
+cudaError_t plane3d_encode(int prec, bool vark, const GridGeo &g, const IterBufs &b,
+                           Plane3dMaps *m);
 GenericPlan generic_plan(int prec, const GridGeo &g, bool vark);
 int generic_partials_needed(const GridGeo &g);
-cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a,
-                                cudaStream_t s);
-cudaError_t add_generic_pass_node(int prec, bool vark, const PassLaunch &a,
-                                  cudaGraph_t body);
+// maps: the handle's tensor maps, required when the plan is the 3D
+// plane-streaming pass (GenericPlan::plane3d), else unused.
+cudaError_t generic_pass_launch(int prec, bool vark, const PassLaunch &a, cudaStream_t s,
+                                const struct Plane3dMaps *maps);
+cudaError_t add_generic_pass_node(int prec, bool vark, const PassLaunch &a, cudaGraph_t body,
+                                  const struct Plane3dMaps *maps);
 
 // Whole solve of a small grid in one CTA (kernels_small.cu): the dynamic
 // shared memory it needs, 0 when the grid does not fit.
