@@ -43,3 +43,19 @@ def test_two_gloo_ranks_aggregate_replicas():
         assert ms_max == pytest.approx(200.0)
         # (1e9 + 2e9) updates in 0.2 s = 15 GLUP/s on every rank
         assert value == pytest.approx(15.0)
+
+
+def test_profiled_traffic_reads_only_a_matching_summary(tmp_path, monkeypatch):
+    # the DRAM traffic of the dominant kernel is reported from the committed
+    # ncu summary only while the kernel sources hash to the recorded value
+    import bench
+    good = tmp_path / "good.md"
+    good.write_text("dram_bytes_per_launch: 1234\nsource_sha256: `%s`\n" % bench.kernel_source_hash())
+    stale = tmp_path / "stale.md"
+    stale.write_text("dram_bytes_per_launch: 1234\nsource_sha256: `%s`\n" % ("0" * 64))
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(good))
+    assert bench.profiled_traffic() == 1234
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(stale))
+    assert bench.profiled_traffic() is None
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(tmp_path / "missing.md"))
+    assert bench.profiled_traffic() is None
