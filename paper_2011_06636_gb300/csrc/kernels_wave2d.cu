@@ -128,9 +128,10 @@ WaveCfg wave_cfg(int prec, int T) {
 
 }  // namespace
 
-// Default depths measured on GB300 at 4096^2: FP32 4 (838 vs 775 GLUP/s at
-// 8), FP32 pair 2 (254 vs 219 GLUP/s at 4): the shallower instantiations fit
-// two CTAs per SM, and occupancy wins over fewer HBM passes.
+// Default depths measured on GB300 at 4096^2 (mixed solve / FP32 leg): FP32
+// pair 2 (1559 ms per solve vs 1710 ms at 4), FP32 4 (1074 vs 976 GLUP/s at
+// 8): the shallower instantiations fit two CTAs per SM, and occupancy wins
+// over fewer HBM passes.
 int wave2d_depth(int prec, int requested) {
     if (prec == PREC_F32) return requested == 8 ? 8 : 4;
     if (prec == PREC_DF) return requested == 4 ? 4 : 2;
