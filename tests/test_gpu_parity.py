@@ -245,6 +245,20 @@ def test_invalid_arguments_return_codes(S):
         S.srj_create([8], level0=30)
 
 
+def test_allocation_failure_reports_enomem(S):
+    # a grid far beyond device memory (4000^3 points, about 1.5 TB of FP64
+    # iterates): the first device allocation fails and srj_create returns
+    # SRJ_ENOMEM with no handle; the library stays usable
+    import ctypes as C
+    L = S.load()
+    g = S._grid([4000, 4000, 4000])
+    hnd = C.c_void_p()
+    assert L.srj_create(C.byref(g), None, None, None, C.byref(hnd)) == S.SRJ_ENOMEM
+    assert not hnd.value
+    h = S.srj_create([16, 16])
+    S.srj_destroy(h)
+
+
 def test_notconv_status_and_cap(S):
     n = [256]
     f = np.ones(256)
