@@ -135,7 +135,21 @@ template <typename T>
 cudaError_t dalloc(T **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return cudaSuccess;
-    return cudaMalloc((void **)p, bytes);
+    const cudaError_t e = cudaMalloc((void **)p, bytes);
+    // a failed allocation also sets the runtime's last-error state, which a
+    // later launch check (cudaGetLastError) would report as its own failure:
+    // the failure is returned here, so clear it
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+}
+
+// pinned host memory, with the same error handling as dalloc
+template <typename T>
+cudaError_t halloc(T **p, size_t bytes) {
+    *p = nullptr;
+    const cudaError_t e = cudaMallocHost((void **)p, bytes);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
 }
 
 void dfree(void *p) {
@@ -770,8 +784,8 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
         ALLOC(h->onorm2, sizeof(double));
     }
 #undef ALLOC
-    if (cudaMallocHost((void **)&h->h_st, sizeof(DevState)) != cudaSuccess ||
-        cudaMallocHost((void **)&h->h_onorm2, sizeof(double)) != cudaSuccess) {
+    if (halloc(&h->h_st, sizeof(DevState)) != cudaSuccess ||
+        halloc(&h->h_onorm2, sizeof(double)) != cudaSuccess) {
         srj_destroy(h);
         return SRJ_ENOMEM;
     }
@@ -1014,7 +1028,7 @@ srj_status srj_create_batched(int32_t nprob, const srj_grid *grids, const srj_st
         dalloc(&B->dprobs, (size_t)nprob * sizeof(BatchProb)) != cudaSuccess ||
         dalloc(&B->dstates, (size_t)nprob * sizeof(BatchState)) != cudaSuccess ||
         dalloc(&B->ndone, sizeof(unsigned int)) != cudaSuccess ||
-        cudaMallocHost((void **)&B->hstates, (size_t)nprob * sizeof(BatchState)) != cudaSuccess) {
+        halloc(&B->hstates, (size_t)nprob * sizeof(BatchState)) != cudaSuccess) {
         srj_destroy(h);
         return SRJ_ENOMEM;
     }
@@ -1192,7 +1206,7 @@ srj_status srj_mg_create(const srj_grid *grid, const srj_stencil *stencil,
     }
     if (dalloc(&m->partials, sizeof(double) * mg_partials_needed()) != cudaSuccess ||
         dalloc(&m->norm2, sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void **)&m->h_norm2, sizeof(double)) != cudaSuccess) {
+        halloc(&m->h_norm2, sizeof(double)) != cudaSuccess) {
         srj_destroy(h);
         return SRJ_ENOMEM;
     }

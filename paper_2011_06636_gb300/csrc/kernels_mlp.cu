@@ -202,6 +202,7 @@ srj_status srj_mlp_forward(const uint16_t *w_host, const float *x_host, int64_t 
         cudaMalloc(&dx, n * kMlpIn * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&dp, n * sizeof(int32_t)) != cudaSuccess ||
         (logits_host && cudaMalloc(&dl, n * kMlpOut * sizeof(float)) != cudaSuccess)) {
+        cudaGetLastError();  // the failure is returned; clear the runtime's last error
         rc = SRJ_ENOMEM;
     } else if (cudaMemcpy(dw, w_host, kMlpParams * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
                    cudaSuccess ||
@@ -236,6 +237,7 @@ srj_status srj_mlp_train(const float *x_dev, const int32_t *y_dev, int64_t n,
     if (cudaMalloc(&m, kMlpParams * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&v, kMlpParams * sizeof(float)) != cudaSuccess ||
         (loss_host && steps > 0 && cudaMalloc(&loss, steps * sizeof(float)) != cudaSuccess)) {
+        cudaGetLastError();  // the failure is returned; clear the runtime's last error
         rc = SRJ_ENOMEM;
     } else {
         TrainArgs a{x_dev, y_dev, order_dev, n, steps, batch, lr, 0.9f, 0.999f, 1e-8f,
