@@ -36,7 +36,7 @@ TOL = 1e-8
 # two-sums (6 each), one exact scaling by 1/4, one FMA and eight plain
 # low-part adds for t (40); then one two-product, one FMA, one two-sum, two
 # adds and one Dekker renormalisation (3) for u + omega t (14).
-DF_OPS_PER_LUP = 54
+DF_OPS_PER_LUP = 46  # FP32 instructions per update of the isotropic FP32-pair form (32 + df_axpy 14)
 WORKLOAD = ("2D Poisson 5-point, 4096x4096 interior, zero Dirichlet, f~U[-1,1] (seed 0+rank), "
             "u0=0, rel residual 1e-8, SRJ scheme family + Alg. 1 heuristic")
 
@@ -329,6 +329,66 @@ def mg_leg(srj, inputs, torch, stream, seed=0, side=4095):
     return out
 
 
+# -------------------------------------------------------- the paper's studies
+def paper_studies_leg(srj, inputs, torch, stream, seed=0):
+    """Two of the paper's out-of-sample studies, timed on the GPU (FP64, the
+    paper's own stopping rules; sweep counts are the ones the parity tests
+    compare with the oracle):
+      * Sec. 4.1: random symmetric diagonally dominant tridiagonal systems,
+        N = 10, 100, 500, 1000, 20 matrices each (seeds 0..19), b = 1,
+        x0 = 0, ||b - A x||_2 < 1e-7; Alg. 1 against the increasing rule;
+      * Sec. 4.2.2: 2D Laplace with homogeneous Neumann boundaries, 256^2 and
+        1024^2 nodes, 10 random starts U[-1,1] each, ||x^n - x^(n-1)||_inf
+        < 1e-10 tested after every sweep; Alg. 1 against the increasing
+        rule."""
+    rules = (("heuristic", srj.SRJ_SEL_HEURISTIC), ("increasing", srj.SRJ_SEL_INCREASING))
+    tri = {}
+    for N in (10, 100, 500, 1000):
+        row = {}
+        for label, sel in rules:
+            sw, secs, ok = [], [], True
+            for m in range(20):
+                d, e = inputs.random_sdd_tridiagonal(N, seed=m)
+                ad = torch.as_tensor(d, device="cuda")
+                ao = torch.as_tensor(e, device="cuda")
+                h = srj.srj_create([N], precision=srj.SRJ_PREC_F64, tol_kind=srj.SRJ_TOL_ABS,
+                                   selector=sel, stream=stream.cuda_stream,
+                                   a_diag_ptr=ad.data_ptr(), a_off_ptrs=[ao.data_ptr()])
+                f = torch.ones(N, dtype=torch.float64, device="cuda")
+                u = torch.zeros_like(f)
+                st = srj.srj_solve(h, f.data_ptr(), u.data_ptr(), 1e-7)
+                srj.srj_destroy(h)
+                sw.append(st["sweeps"])
+                secs.append(st["seconds"])
+                ok = ok and st["status"] == srj.SRJ_OK
+            row[label] = {"mean_sweeps": sum(sw) / len(sw), "mean_solve_ms": 1e3 * sum(secs) / len(secs),
+                          "all_converged": ok}
+        row["increasing_over_heuristic"] = (row["increasing"]["mean_sweeps"]
+                                            / row["heuristic"]["mean_sweeps"])
+        tri["N=%d" % N] = row
+    lap = {}
+    for side in (256, 1024):
+        n = [side, side]
+        f = torch.zeros(side * side, dtype=torch.float64, device="cuda")
+        row = {}
+        for label, sel in rules:
+            h = srj.srj_create(n, bc=[srj.SRJ_BC_NEUMANN] * 2, precision=srj.SRJ_PREC_F64,
+                               tol_kind=srj.SRJ_TOL_DINF, selector=sel, stream=stream.cuda_stream)
+            sw, secs, ok = [], [], True
+            for trial in range(10):
+                u = torch.as_tensor(inputs.uniform_rhs(n, seed=seed + trial).ravel(), device="cuda")
+                st = srj.srj_solve(h, f.data_ptr(), u.data_ptr(), 1e-10)
+                sw.append(st["sweeps"])
+                secs.append(st["seconds"])
+                ok = ok and st["status"] == srj.SRJ_OK
+            srj.srj_destroy(h)
+            mean_s = sum(secs) / len(secs)
+            row[label] = {"mean_sweeps": sum(sw) / len(sw), "mean_solve_s": mean_s,
+                          "glups": sum(sw) * side * side / sum(secs) / 1e9, "all_converged": ok}
+        lap["%dx%d" % (side, side)] = row
+    return {"random_tridiagonal_sec4_1": tri, "laplace_neumann_sec4_2_2": lap}
+
+
 # ----------------------------------------------------------- learned selector
 def selector_leg(srj, inputs, torch, stream, seed=0):
     """Unseen problems for the learned selector: 2D anisotropic (eps_x = 0.01)
@@ -549,6 +609,9 @@ def run_ours(args, rank, world):
     if not args.no_mg:
         mg = mg_leg(srj, inputs, torch, stream, seed=rank)
         mg["srj_mixed_4096_time_to_tol_s"] = ms_max / args.steps / 1e3
+    studies = None
+    if not args.no_paper:
+        studies = paper_studies_leg(srj, inputs, torch, stream, seed=rank)
     vark = None
     if args.with_3d:
         vark = vark3d_leg(srj, inputs, torch, stream, seed=rank, side=args.side3d,
@@ -598,6 +661,7 @@ def run_ours(args, rank, world):
             "batched": batched,
             "learned_selector": sel,
             "multigrid_srj_smoother": mg,
+            "paper_studies": studies,
             "vark3d": vark,
             "mixed_vs_plain_speedup": (fp64["time_to_tol_s"] / (ms_max / args.steps / 1e3))
             if fp64 else None,
@@ -620,6 +684,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-selector", action="store_true")
     ap.add_argument("--no-mg", action="store_true", help="skip the multigrid leg")
+    ap.add_argument("--no-paper", action="store_true",
+                    help="skip the Sec. 4.1 / Sec. 4.2.2 studies")
     ap.add_argument("--with-3d", action="store_true", help="add the 3D variable-k leg")
     ap.add_argument("--side3d", type=int, default=512)
     ap.add_argument("--f32-depth", type=int, default=0, help="temporal depth of the FP32 leg")

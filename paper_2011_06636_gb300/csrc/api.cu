@@ -709,10 +709,8 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
         if (e < 0 || !std::isfinite(e)) return bad("eps");
         ee[a] = e > 0 ? e : 1.0;
     }
-    g.cx = ee[0] / (hh[0] * hh[0]);
-    g.cy = g.dim > 1 ? ee[1] / (hh[1] * hh[1]) : 0.0;
-    g.cz = g.dim > 2 ? ee[2] / (hh[2] * hh[2]) : 0.0;
-    g.diag = 2.0 * (g.cx + g.cy + g.cz);
+    geo_set_coefficients(g, ee[0] / (hh[0] * hh[0]), g.dim > 1 ? ee[1] / (hh[1] * hh[1]) : 0.0,
+                         g.dim > 2 ? ee[2] / (hh[2] * hh[2]) : 0.0);
     g.neu = neu;
     g.pitch = ((long long)g.nx + 31) / 32 * 32;
     g.plane = g.pitch * g.ny;
@@ -1013,10 +1011,7 @@ srj_status srj_create_batched(int32_t nprob, const srj_grid *grids, const srj_st
         const double hy = grids[p].h[1] > 0 ? grids[p].h[1] : 1.0 / (g.ny + 1.0);
         const double ex = stencils && stencils[p].eps[0] > 0 ? stencils[p].eps[0] : 1.0;
         const double ey = stencils && stencils[p].eps[1] > 0 ? stencils[p].eps[1] : 1.0;
-        g.cx = ex / (hx * hx);
-        g.cy = ey / (hy * hy);
-        g.cz = 0.0;
-        g.diag = 2.0 * (g.cx + g.cy);
+        geo_set_coefficients(g, ex / (hx * hx), ey / (hy * hy), 0.0);
         g.pitch = ((long long)g.nx + 31) / 32 * 32;
         g.plane = g.pitch * g.ny;
         B->npts[p] = (long long)g.nx * g.ny;

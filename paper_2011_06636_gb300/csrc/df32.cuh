@@ -63,20 +63,30 @@ __device__ __forceinline__ df32 df_t2d(df32 w, df32 e, df32 s, df32 n, float ax,
     return df32{r2.hi, lo};
 }
 
-// The isotropic case ax = ay = 1/4 (equal spacing and coefficients): the
-// scaling by 1/4 is exact, so the four neighbours are summed first and no
-// product error terms arise.  40 FP32 operations.
-__device__ __forceinline__ df32 df_t2d_iso(df32 w, df32 e, df32 s, df32 n, float g, df32 u) {
-    const df32 sx = df_two_sum(w.hi, e.hi);
-    const float sxl = __fadd_rn(sx.lo, __fadd_rn(w.lo, e.lo));
-    const df32 sy = df_two_sum(s.hi, n.hi);
-    const float syl = __fadd_rn(sy.lo, __fadd_rn(s.lo, n.lo));
-    const df32 q = df_two_sum(sx.hi, sy.hi);
-    const float ql = __fadd_rn(q.lo, __fadd_rn(sxl, syl));
-    const df32 r1 = df_two_sum(__fmul_rn(q.hi, 0.25f), g);
+// Sum of two FP32 pairs with an unnormalised result: the high parts by an
+// error-free sum, the low parts and its error added plainly.  8 FP32
+// operations.
+__device__ __forceinline__ df32 df_pair_sum(df32 a, df32 b) {
+    const df32 s = df_two_sum(a.hi, b.hi);
+    return df32{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+
+// The isotropic case ax = ay = 1/4 (equal spacing and coefficients) from two
+// pair sums p and q that together hold the four neighbours: the scaling by
+// 1/4 is exact, so no product error terms arise.  24 FP32 operations.
+__device__ __forceinline__ df32 df_t2d_iso_pairs(df32 p, df32 q, float g, df32 u) {
+    const df32 s = df_pair_sum(p, q);
+    const df32 r1 = df_two_sum(__fmul_rn(s.hi, 0.25f), g);
     const df32 r2 = df_two_sum(r1.hi, -u.hi);
-    const float lo = __fsub_rn(__fadd_rn(__fmaf_rn(ql, 0.25f, r1.lo), r2.lo), u.lo);
+    const float lo = __fsub_rn(__fadd_rn(__fmaf_rn(s.lo, 0.25f, r1.lo), r2.lo), u.lo);
     return df32{r2.hi, lo};
+}
+
+// The isotropic case from the four neighbours: 40 FP32 operations (the pass
+// kernels share each diagonal pair sum between two points instead, 32 per
+// point: see wave_item.cuh).
+__device__ __forceinline__ df32 df_t2d_iso(df32 w, df32 e, df32 s, df32 n, float g, df32 u) {
+    return df_t2d_iso_pairs(df_pair_sum(w, e), df_pair_sum(s, n), g, u);
 }
 
 // Variable-coefficient sweep residual in FP32-pair arithmetic:

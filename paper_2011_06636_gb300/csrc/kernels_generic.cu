@@ -26,10 +26,12 @@ constexpr int kBlock = 256;
 
 // ---------------------------------------------------------- the pass kernel
 // Thread (tx, ty) of a CTA owns grid column (x, y) and walks z through
-// [z0, z0 + zchunk); the z neighbours rotate through registers, the x and y
-// neighbours come through L1.  1D grids use 256x1 blocks.
+// [z0, z0 + chunk); the z neighbours rotate through registers, the x and y
+// neighbours come through L1.  On 2D grids the thread instead takes rows
+// y0 + ty, y0 + ty + 8, ... of a band of 8 * chunk rows (fewer CTAs, so fewer
+// partials for the last CTA to fold).  1D grids use 256x1 blocks.
 template <int PREC, int DIM, bool VARK>
-__global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int zchunk) {
+__global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int chunk) {
     using T = typename Elem<PREC>::T;
     using C = typename Elem<PREC>::C;
     using P = Point<PREC, DIM>;
@@ -51,24 +53,27 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
 
     const GridGeo &g = a.geo;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int zchunk = DIM > 2 ? chunk : 1;
+    const int rows = DIM == 2 ? chunk : 1;  // rows per thread
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
-    const bool active = (x < g.nx) && (y < g.ny);
     const int src = p.cur, dst = p.cur ^ 1;
     const C *f = (const C *)a.bufs.f;
 
-    C cconst[3], invd_c = C(1.0 / g.diag), diag_c = C(g.diag);
-    cconst[0] = C(g.cx / g.diag);
-    cconst[1] = C(g.cy / g.diag);
-    cconst[2] = C(g.cz / g.diag);
+    C cconst[3], invd_c = C(g.invdiag), diag_c = C(g.diag);
+    cconst[0] = C(g.acx);
+    cconst[1] = C(g.acy);
+    cconst[2] = C(g.acz);
 
-    double part = 0.0;
+    double part = 0.0;  // residual sum (resid pass)
+    long long dbits = 0;  // largest |u' - u| of the sweep (abs_diff_bits)
     // Neumann axes (Sec. 4.2.2): the ghost node one step outside mirrors the
     // node one step inside; Dirichlet axes read zero there
     const bool nx_ = g.neu & 1, ny_ = g.neu & 2, nz_ = g.neu & 4;
     const bool dinf = a.dinf && p.nsw;
-    if (active) {
+    for (int r = 0; r < rows; ++r) {
+        const int y = (blockIdx.y * rows + r) * blockDim.y + threadIdx.y;
+        if (x >= g.nx || y >= g.ny) break;
         const long long col = (long long)x + g.pitch * y;
         T u_zm = (DIM > 2 && z0 > 0) ? load_u<PREC>(a.bufs, src, col + g.plane * (z0 - 1))
                                      : zero_u<PREC>();
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
                 const T un = P::relax(u_c, t, omega);
                 store_u<PREC>(a.bufs, dst, i, un);
                 if constexpr (PREC != PREC_DF)
-                    if (dinf) part = nan_max(part, fabs((double)un - (double)u_c));
+                    if (dinf) dbits = max_bits(dbits, abs_diff_bits((double)un, (double)u_c));
             } else {
                 part += P::resid2(t, diag_i);
             }
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
     }
     double tot = 0.0;
     if (p.resid) tot = block_sum(part);
-    else if (dinf) tot = block_max(part);
+    else if (dinf) tot = block_max_bits(dbits);
     finish_pass(a, p, tot, dinf);
 }
 
@@ -174,9 +179,19 @@ GenericPlan generic_plan(int prec, const GridGeo &g, bool vark) {
         p.block = dim3(kBlock, 1, 1);
         p.zchunk = 1;
         p.grid = dim3((g.nx + kBlock - 1) / kBlock, 1, 1);
+    } else if (g.dim == 2) {
+        // bands of 8 * rows rows, rows chosen so that the grid stays within
+        // 16 CTAs per SM
+        p.block = dim3(32, kBlock / 32, 1);
+        const long long bx = (g.nx + 31) / 32, by = (g.ny + p.block.y - 1) / p.block.y;
+        const long long cap = 152 * 16;
+        long long rows = (bx * by + cap - 1) / cap;
+        if (rows < 1) rows = 1;
+        p.zchunk = (int)rows;
+        p.grid = dim3((unsigned)bx, (unsigned)((by + rows - 1) / rows), 1);
     } else {
         p.block = dim3(32, kBlock / 32, 1);
-        p.zchunk = g.dim == 3 ? (g.nz < 32 ? g.nz : 32) : 1;
+        p.zchunk = g.nz < 32 ? g.nz : 32;
         p.grid = dim3((g.nx + 31) / 32, (g.ny + p.block.y - 1) / p.block.y,
                       (g.nz + p.zchunk - 1) / p.zchunk);
     }

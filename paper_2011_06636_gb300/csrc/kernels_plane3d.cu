@@ -161,17 +161,18 @@ __global__ void __launch_bounds__(kTX * kTY)
             return *(const T *)(s + L::o_hi + c * ES);
     };
 
-    C cconst[3], invd_c = C(1.0 / g.diag), diag_c = C(g.diag);
-    cconst[0] = C(g.cx / g.diag);
-    cconst[1] = C(g.cy / g.diag);
-    cconst[2] = C(g.cz / g.diag);
+    C cconst[3], invd_c = C(g.invdiag), diag_c = C(g.diag);
+    cconst[0] = C(g.acx);
+    cconst[1] = C(g.acy);
+    cconst[2] = C(g.acz);
 
     if (tid == 0)
         for (int zz = z0 - 1; zz < z0 + kPD; ++zz) issue(zz);
     const int gx = x0 + tx, gy = y0 + ty;
     const bool active = gx < g.nx && gy < g.ny;
     const long long col = (long long)gx + g.pitch * gy;
-    double part = 0.0;
+    double part = 0.0;  // residual sum (resid pass)
+    long long dbits = 0;  // largest |u' - u| of the sweep (abs_diff_bits)
     int last_issued = z0 + kPD - 1;  // planes issued so far: z0 - 1 .. last_issued
     int next_wait = z0 - 1;          // first plane not yet waited for
     bool ok = true;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kTX * kTY)
                 const T un = P::relax(u_c, t, omega);
                 store_u<PREC>(a.bufs, dst, i, un);
                 if constexpr (PREC != PREC_DF)
-                    if (dinf) part = nan_max(part, fabs((double)un - (double)u_c));
+                    if (dinf) dbits = max_bits(dbits, abs_diff_bits((double)un, (double)u_c));
             } else {
                 part += P::resid2(t, diag_i);
             }
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kTX * kTY)
     if (s_err && tid == 0) atomicExch(&a.st->status, (int)DST_TIMEOUT);
     double tot = 0.0;
     if (p.resid) tot = block_sum(part);
-    else if (dinf) tot = block_max(part);
+    else if (dinf) tot = block_max_bits(dbits);
     finish_pass(a, p, tot, dinf);
 }
 

@@ -79,10 +79,10 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(PassLaunch a
             sid[i] = ((const C *)a.bufs.invd)[q];
         }
     }
-    C cconst[3], invd_c = C(1.0 / g.diag), diag_c = C(g.diag);
-    cconst[0] = C(g.cx / g.diag);
-    cconst[1] = C(g.cy / g.diag);
-    cconst[2] = C(g.cz / g.diag);
+    C cconst[3], invd_c = C(g.invdiag), diag_c = C(g.diag);
+    cconst[0] = C(g.acx);
+    cconst[1] = C(g.acy);
+    cconst[2] = C(g.acz);
     const bool nx_ = g.neu & 1, ny_ = g.neu & 2, nz_ = g.neu & 4;
     __syncthreads();
 
@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(PassLaunch a
             if constexpr (LO) return df32{s_hi[src][j], s_lo[src][j]};
             else return s_hi[src][j];
         };
-        double part = 0.0;
+        double part = 0.0;  // residual sum (resid pass)
+        long long dbits = 0;  // largest |u' - u| of the sweep (abs_diff_bits)
         for (int i = tid; i < n; i += kSmallThreads) {
             const int x = i % nx, yz = i / nx;
             const int y = yz % ny, z = yz / ny;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(PassLaunch a
                     s_hi[dst][i] = un;
                 }
                 if constexpr (PREC != PREC_DF)
-                    if (dinf) part = nan_max(part, fabs((double)un - (double)uc));
+                    if (dinf) dbits = max_bits(dbits, abs_diff_bits((double)un, (double)uc));
             } else {
                 part += P::resid2(t, diag_i);
             }
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(PassLaunch a
         // end of the iteration orders the sweep before the next one)
         double tot = 0.0;
         if (p.resid) tot = block_sum(part);
-        else if (dinf) tot = block_max(part);
+        else if (dinf) tot = block_max_bits(dbits);
         int pick = -1;
         if (tid < 32) {  // the reductions leave the total in thread 0 only
             const double t0 = __shfl_sync(0xffffffffu, tot, 0);

@@ -180,23 +180,29 @@ __device__ __forceinline__ double block_sum(double v) {
     return t;  // valid in thread 0
 }
 
-// max that keeps a NaN (fmax would drop it)
-__device__ __forceinline__ double nan_max(double a, double b) {
-    return (b > a || b != b) ? b : a;
+// |a - b| as the bit pattern of a non-negative double.  Such patterns order
+// like the values they encode, and a NaN (exponent all ones, mantissa not
+// zero) lies above +inf, so an integer max of them is the largest change with
+// a NaN kept, taken on the integer units instead of FP64 compares (FP64 issues
+// at a small fraction of the FP32 rate on this part).
+__device__ __forceinline__ long long abs_diff_bits(double a, double b) {
+    return __double_as_longlong(a - b) & 0x7fffffffffffffffLL;
 }
 
-// Block max with NaN kept (order-independent, so deterministic).
-__device__ __forceinline__ double block_max(double v) {
-    __shared__ double s_warp[32];
+__device__ __forceinline__ long long max_bits(long long a, long long b) { return a > b ? a : b; }
+
+// Block max of abs_diff_bits values, returned as the double (valid in thread 0).
+__device__ __forceinline__ double block_max_bits(long long v) {
+    __shared__ long long s_wbits[32];
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int nthreads = blockDim.x * blockDim.y;
-    for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((tid & 31) == 0) s_warp[tid >> 5] = v;
+    for (int o = 16; o > 0; o >>= 1) v = max_bits(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((tid & 31) == 0) s_wbits[tid >> 5] = v;
     __syncthreads();
-    double t = 0.0;
+    long long t = 0;
     if (tid == 0)
-        for (int w = 0; w < (nthreads + 31) / 32; ++w) t = nan_max(t, s_warp[w]);
-    return t;  // valid in thread 0
+        for (int w = 0; w < (nthreads + 31) / 32; ++w) t = max_bits(t, s_wbits[w]);
+    return __longlong_as_double(t);
 }
 
 // Ticket + last-CTA finish, shared by all pass kernels.  block_total is the
@@ -219,22 +225,24 @@ __device__ void finish_pass(const PassLaunch &a, const PassPlan &p, double block
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // the whole CTA folds the partials (written by other CTAs: read from L2),
+    // each thread a fixed stride of them, then the block in a fixed order:
+    // deterministic for a given grid
+    const int nthreads = blockDim.x * blockDim.y;
     double norm2 = 0.0, dmax = -1.0;
-    if (p.resid && tid < 32) {
-        // fixed assignment of partials to lanes, fixed butterfly: deterministic
+    if (p.resid) {
         double acc = 0.0;
-        const volatile double *part = a.partials;
-        for (unsigned int i = tid; i < nblocks; i += 32) acc += part[i];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        norm2 = acc;
+#pragma unroll 4
+        for (unsigned int i = tid; i < nblocks; i += nthreads) acc += __ldcg(a.partials + i);
+        norm2 = block_sum(acc);
+    } else if (dpass) {
+        long long acc = 0;
+#pragma unroll 4
+        for (unsigned int i = tid; i < nblocks; i += nthreads)
+            acc = max_bits(acc, __double_as_longlong(__ldcg(a.partials + i)));
+        dmax = block_max_bits(acc);
     }
-    if (dpass && tid < 32) {
-        double acc = 0.0;
-        const volatile double *part = a.partials;
-        for (unsigned int i = tid; i < nblocks; i += 32) acc = nan_max(acc, part[i]);
-        for (int o = 16; o > 0; o >>= 1) acc = nan_max(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-        dmax = acc;
-    }
+    if (tid < 32) norm2 = __shfl_sync(0xffffffffu, norm2, 0);  // block totals sit in thread 0
     int pick = -1;
     if (tid < 32) pick = mlp_pick_at_cycle_end(a.st, a.cfg, p, norm2, a.lvl_m, tid);
     if (tid == 0) {

@@ -109,7 +109,22 @@ struct GridGeo {
     double diag;        // 2 (cx + cy + cz) for constant coefficients
     int32_t neu;        // bit a set: axis a has mirrored-ghost Neumann ends (Sec. 4.2.2)
     int32_t pad;
+    // 1 / diag and c_a / diag, divided once on the host (FP64 division is
+    // slow on the device and the kernels need them per thread)
+    double invdiag, acx, acy, acz;
 };
+
+// Sets the axis coefficients of g and the values derived from them.
+inline void geo_set_coefficients(GridGeo &g, double cx, double cy, double cz) {
+    g.cx = cx;
+    g.cy = cy;
+    g.cz = cz;
+    g.diag = 2.0 * (cx + cy + cz);
+    g.invdiag = 1.0 / g.diag;
+    g.acx = cx / g.diag;
+    g.acy = cy / g.diag;
+    g.acz = cz / g.diag;
+}
 
 enum Prec : int32_t { PREC_F64 = 0, PREC_F32 = 1, PREC_DF = 2 };
 
@@ -144,7 +159,7 @@ struct PassLaunch {
 // error of the launch (cudaSuccess when queued).
 struct GenericPlan {
     dim3 grid, block;
-    int zchunk;
+    int zchunk;    // z planes per thread (3D), rows per thread (2D)
     void *kernel;  // __global__ entry for graph nodes
     int smem;      // dynamic shared memory bytes
     int plane3d;   // 1: the 3D plane-streaming kernel (kernels_plane3d.cu)

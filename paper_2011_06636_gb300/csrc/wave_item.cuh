@@ -194,6 +194,13 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
         for (int q = 0; q < 3; ++q)
 #pragma unroll
             for (int v = 0; v < V; ++v) ring[s][q][v] = zero_u<PREC>();
+    // isotropic FP32-pair form: each level's diagonal pair sums of the row it
+    // computed at the previous step (see the level loop)
+    E pprev[ISO ? T : 1][V];
+#pragma unroll
+    for (int s = 0; s < (ISO ? T : 1); ++s)
+#pragma unroll
+        for (int v = 0; v < V; ++v) pprev[s][v] = zero_u<PREC>();
     float kahan_s = 0.f, kahan_c = 0.f;  // FP32 paths: compensated r^2 sum
     double dsum = 0.0;                   // FP64 path
 
@@ -285,7 +292,9 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
         // t-1, t-2, t-3 and writes its row of step t into slot S3
 #pragma unroll
         for (int s = T; s >= 1; --s) {
-            if (CHK && t < 3 * s) continue;           // above every needed row
+            // above every needed row (the isotropic form starts one step early:
+            // the first needed row takes the pair sums of the row before it)
+            if (CHK && t < 3 * s - (ISO ? 1 : 0)) continue;
             if (CHK && t > nload - 1 + s) continue;   // below every needed row
             const int row = jt - dir * (2 * s);
             // identity level: only in the last pass of a cycle (a pass without
@@ -298,20 +307,43 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
             const int fs = (t - 2 * s) & (W::FR - 1);
             C fv[V];
             load_vec(fring, fs, fv);
-            const E left = shfl_left(ring[s - 1][S2][V - 1]);
-            const E right = shfl_right(ring[s - 1][S2][0]);
+            if constexpr (ISO) {
+                // Row r = j(t) - 2 s dir with the four neighbours grouped in
+                // diagonal pairs: p(x) = u(x+1, r) + u(x, r + dir) from the rows
+                // of steps t-2 and t-1, and the partner pair u(x-1, r) +
+                // u(x, r - dir), which is p(x-1) of row r - dir: this level's
+                // pair sums of the previous step.  One pair sum per point
+                // instead of two.
+                const E right = shfl_right(ring[s - 1][S2][0]);
+                const E pleft = shfl_left(pprev[s - 1][V - 1]);
+                E pc[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                E nb[6];
-                nb[0] = v > 0 ? ring[s - 1][S2][v - 1] : left;
-                nb[1] = v < V - 1 ? ring[s - 1][S2][v + 1] : right;
-                nb[2] = ring[s - 1][S3][v];
-                nb[3] = ring[s - 1][S1][v];
-                const E uc = ring[s - 1][S2][v];
-                E tt;
-                if constexpr (ISO) tt = Point<PREC, 2>::t_const_iso(nb, fv[v], uc);
-                else tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fv[v], uc);
-                ring[s][S3][v] = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
+                for (int v = 0; v < V; ++v)
+                    pc[v] = df_pair_sum(v < V - 1 ? ring[s - 1][S2][v + 1] : right,
+                                        ring[s - 1][S1][v]);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const E uc = ring[s - 1][S2][v];
+                    const E tt = df_t2d_iso_pairs(pc[v], v > 0 ? pprev[s - 1][v - 1] : pleft,
+                                                  fv[v], uc);
+                    ring[s][S3][v] = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) pprev[s - 1][v] = pc[v];
+            } else {
+                const E left = shfl_left(ring[s - 1][S2][V - 1]);
+                const E right = shfl_right(ring[s - 1][S2][0]);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    E nb[6];
+                    nb[0] = v > 0 ? ring[s - 1][S2][v - 1] : left;
+                    nb[1] = v < V - 1 ? ring[s - 1][S2][v + 1] : right;
+                    nb[2] = ring[s - 1][S3][v];
+                    nb[3] = ring[s - 1][S1][v];
+                    const E uc = ring[s - 1][S2][v];
+                    const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fv[v], uc);
+                    ring[s][S3][v] = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
+                }
             }
             // Dirichlet ghosts stay zero (a warp-uniform test: the row is the
             // same for every lane and `edge` is per strip)
@@ -442,9 +474,9 @@ __device__ __forceinline__ void fill_ctx(ItemCtx<PREC, T> &c, const GridGeo &g,
     c.nsw = nsw;
     c.resid = resid;
     c.diag = C(g.diag);
-    c.invd = C(1.0 / g.diag);
-    c.acoef[0] = C(g.cx / g.diag);
-    c.acoef[1] = C(g.cy / g.diag);
+    c.invd = C(g.invdiag);
+    c.acoef[0] = C(g.acx);
+    c.acoef[1] = C(g.acy);
     c.acoef[2] = C(0);
     c.iso = PREC == PREC_DF && c.acoef[0] == C(0.25) && c.acoef[1] == C(0.25);
 }
