@@ -176,6 +176,12 @@ __global__ void __launch_bounds__(kTX * kTY)
     int last_issued = z0 + kPD - 1;  // planes issued so far: z0 - 1 .. last_issued
     int next_wait = z0 - 1;          // first plane not yet waited for
     bool ok = true;
+    // ring slots of planes z - 1, z, z + 1 (advanced with z, no modulo)
+    int im = 0, i0 = 1 % kNS, ip = 2 % kNS;
+    // the column's iterate at z - 1 and z and its -z face weight carry over
+    // in registers from the previous plane
+    T u_m = zero_u<PREC>(), u_c = zero_u<PREC>();
+    C wz_m = C(0);
     for (int z = z0; z < z1; ++z) {
         for (; next_wait <= z + 1; ++next_wait) ok = ok && wait(next_wait);
         // one decision for the whole block (a bounded wait may run out in one
@@ -187,30 +193,35 @@ __global__ void __launch_bounds__(kTX * kTY)
         }
         if (tid == 0) issue(z + kPD);
         last_issued = z + kPD;
-        const unsigned char *sm = slot(z - 1), *s0 = slot(z), *sp = slot(z + 1);
+        const unsigned char *sm = smem + im * L::BYTES, *s0 = smem + i0 * L::BYTES,
+                            *sp = smem + ip * L::BYTES;
         if (active) {
+            if (z == z0) {
+                u_m = ldu(sm, tx, ty);
+                u_c = ldu(s0, tx, ty);
+                if constexpr (VARK) wz_m = ld(sm, L::o_wz, tid);
+            }
             T nb[6];
             nb[0] = ldu(s0, tx - 1, ty);
             nb[1] = ldu(s0, tx + 1, ty);
             nb[2] = ldu(s0, tx, ty - 1);
             nb[3] = ldu(s0, tx, ty + 1);
-            nb[4] = ldu(sm, tx, ty);
+            nb[4] = u_m;
             nb[5] = ldu(sp, tx, ty);
-            const T u_c = ldu(s0, tx, ty);
             const C fi = ld(s0, L::o_f, tid);
             T t;
-            C diag_i = diag_c;
+            C invd_i = invd_c;
             if constexpr (VARK) {
                 C wgt[6];
                 wgt[0] = ld(s0, L::o_wx, ty * kSX + kHX + tx - 1);
                 wgt[1] = ld(s0, L::o_wx, ty * kSX + kHX + tx);
                 wgt[2] = ld(s0, L::o_wy, ty * kTX + tx);
                 wgt[3] = ld(s0, L::o_wy, (ty + 1) * kTX + tx);
-                wgt[4] = ld(sm, L::o_wz, tid);
+                wgt[4] = wz_m;
                 wgt[5] = ld(s0, L::o_wz, tid);
-                const C invd_i = ld(s0, L::o_id, tid);
+                wz_m = wgt[5];
+                invd_i = ld(s0, L::o_id, tid);
                 t = P::t_of(nb, wgt, invd_i, fi, u_c);
-                diag_i = C(1) / invd_i;
             } else {
                 t = P::t_const(nb, cconst, invd_c, fi, u_c);
             }
@@ -221,9 +232,14 @@ __global__ void __launch_bounds__(kTX * kTY)
                 if constexpr (PREC != PREC_DF)
                     if (dinf) dbits = max_bits(dbits, abs_diff_bits((double)un, (double)u_c));
             } else {
-                part += P::resid2(t, diag_i);
+                part += P::resid2(t, VARK ? C(1) / invd_i : diag_c);
             }
+            u_m = u_c;
+            u_c = nb[5];
         }
+        im = i0;
+        i0 = ip;
+        ip = ip + 1 == kNS ? 0 : ip + 1;
     }
     // copies still in flight land before the CTA's shared memory goes away
     // (each wait is bounded); a wait that ran out marks the solve
