@@ -113,6 +113,25 @@ struct Point {
         return df_t2d_iso(nb[0], nb[1], nb[2], nb[3], f, uc);
     }
 
+    // 2D isotropic case a_x = a_y = 1/4 from two pair sums p, q that together
+    // hold the four neighbours (the wave kernel shares each pair sum between
+    // two points): FP32 pair 8 + 24 operations with the scaled right-hand
+    // side (invd unused); FP64 t = fma(1/4, p + q, fma(invd, f, -u_c)), with
+    // the pair sum 4 FP64 instructions instead of 6.
+    __device__ __forceinline__ static T pair_sum(T a, T b) {
+        if constexpr (PREC == PREC_DF) return df_pair_sum(a, b);
+        else return a + b;
+    }
+    __device__ __forceinline__ static T t_iso_pairs(T p, T q, C invd, C f, T uc) {
+        static_assert(DIM == 2, "isotropic form: 2D only");
+        if constexpr (PREC == PREC_DF) {
+            (void)invd;
+            return df_t2d_iso_pairs(p, q, f, uc);
+        } else {
+            return fma(C(0.25), p + q, fma(invd, f, -uc));
+        }
+    }
+
     __device__ __forceinline__ static T relax(T uc, T t, double omega) {
         if constexpr (PREC == PREC_DF) return df_axpy(uc, t, (float)omega);
         else return uc + (C)omega * t;

@@ -125,7 +125,7 @@ struct ItemCtx {
     C omega[T];
     int nsw;     // sweeps of this pass (levels beyond nsw are identities)
     int resid;   // 1: accumulate the residual of the final state
-    int iso;     // FP32 pair with acoef = {1/4, 1/4}: the isotropic stencil form
+    int iso;     // FP32 pair or FP64 with acoef = {1/4, 1/4}: the isotropic stencil form
     C diag, invd, acoef[3];
 };
 
@@ -194,8 +194,8 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
         for (int q = 0; q < 3; ++q)
 #pragma unroll
             for (int v = 0; v < V; ++v) ring[s][q][v] = zero_u<PREC>();
-    // isotropic FP32-pair form: each level's diagonal pair sums of the row it
-    // computed at the previous step (see the level loop)
+    // isotropic form: each level's diagonal pair sums of the row it computed
+    // at the previous step (see the level loop)
     E pprev[ISO ? T : 1][V];
 #pragma unroll
     for (int s = 0; s < (ISO ? T : 1); ++s)
@@ -270,7 +270,7 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
                     nb[2] = ring[T][S3][v];
                     nb[3] = ring[T][S1][v];
                     E tt;
-                    if constexpr (ISO) tt = Point<PREC, 2>::t_const_iso(nb, fvv, ring[T][S2][v]);
+                    if constexpr (ISO && LO) tt = Point<PREC, 2>::t_const_iso(nb, fvv, ring[T][S2][v]);
                     else tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fvv, ring[T][S2][v]);
                     if constexpr (PREC == PREC_F64) {
                         const double r = c.diag * tt;
@@ -319,13 +319,13 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
                 E pc[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v)
-                    pc[v] = df_pair_sum(v < V - 1 ? ring[s - 1][S2][v + 1] : right,
-                                        ring[s - 1][S1][v]);
+                    pc[v] = Point<PREC, 2>::pair_sum(v < V - 1 ? ring[s - 1][S2][v + 1] : right,
+                                                     ring[s - 1][S1][v]);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const E uc = ring[s - 1][S2][v];
-                    const E tt = df_t2d_iso_pairs(pc[v], v > 0 ? pprev[s - 1][v - 1] : pleft,
-                                                  fv[v], uc);
+                    const E tt = Point<PREC, 2>::t_iso_pairs(
+                        pc[v], v > 0 ? pprev[s - 1][v - 1] : pleft, c.invd, fv[v], uc);
                     ring[s][S3][v] = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
                 }
 #pragma unroll
@@ -439,11 +439,12 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
 }
 
 // The residual level is compiled only into the variant for the last pass of
-// a cycle, the isotropic FP32-pair form only into the FP32-pair variants.
+// a cycle, the isotropic form only into the FP32-pair and FP64 variants (the
+// FP32 pass is bound by memory, not arithmetic).
 template <int PREC, int T>
 __device__ __forceinline__ double wave_item(const ItemCtx<PREC, T> &c, int strip, int y0, int y1,
                                             int dir, unsigned char *wbase, int lane) {
-    if constexpr (PREC == PREC_DF) {
+    if constexpr (PREC == PREC_DF || PREC == PREC_F64) {
         if (c.iso) {
             if (c.resid) return wave_item_impl<PREC, T, true, true>(c, strip, y0, y1, dir, wbase, lane);
             return wave_item_impl<PREC, T, false, true>(c, strip, y0, y1, dir, wbase, lane);
@@ -478,7 +479,8 @@ __device__ __forceinline__ void fill_ctx(ItemCtx<PREC, T> &c, const GridGeo &g,
     c.acoef[0] = C(g.acx);
     c.acoef[1] = C(g.acy);
     c.acoef[2] = C(0);
-    c.iso = PREC == PREC_DF && c.acoef[0] == C(0.25) && c.acoef[1] == C(0.25);
+    c.iso = (PREC == PREC_DF || PREC == PREC_F64) && c.acoef[0] == C(0.25) &&
+            c.acoef[1] == C(0.25);
 }
 
 }  // namespace
