@@ -110,6 +110,22 @@ def test_dinf_stop_closed_form_on_gpu(S, orc, level, k, tol):
     assert st["status"] == S.SRJ_OK and st["sweeps"] == s_exp
 
 
+def test_generic_pass_with_several_rows_per_thread(S, orc):
+    # 1030 x 700 nodes: 33 x 88 column tiles of 32 x 8, more than 16 per SM,
+    # so each thread of the one-sweep pass takes two rows (ragged in both
+    # axes); the per-sweep stop folds the block maxima of 33 x 44 CTAs
+    n = [1030, 700]
+    P = orc.Problem(n, bc=[1, 1])
+    f = np.zeros(P.size)
+    u0 = inputs.uniform_rhs(n, seed=11).ravel()
+    ref = orc.srj_solve(P, f, u0, tol=1e-4, tol_kind="dinf")
+    st, u, lv, rn = _solve(S, n, [1, 1], f, u0, 1e-4, S.SRJ_TOL_DINF)
+    assert ref["status"] == 0 and st["status"] == S.SRJ_OK
+    np.testing.assert_array_equal(lv, ref["levels"])
+    assert st["sweeps"] == ref["sweeps"] and st["cycles"] == ref["cycles"]
+    np.testing.assert_allclose(u, ref["u"], rtol=0, atol=1e-12 * np.abs(ref["u"]).max())
+
+
 def test_dinf_dirichlet_f32(S, orc):
     # the per-sweep test in FP32: the stop lands within a sweep or two of the
     # FP64 oracle's and the solution within FP32 accuracy of it

@@ -131,6 +131,29 @@ def test_fixed_schedule_f64(S, orc, name, n, eps, kind):
     assert np.all(np.abs(rn - rno) <= 1e-10 * rno + 1e-13 * r0)
 
 
+def test_fixed_schedule_2d_vark_several_rows_per_thread(S, orc):
+    """Variable k on 1030 x 700 points: more column tiles than 16 CTAs per SM,
+    so each thread of the 2D one-sweep pass takes two rows (ragged in both
+    axes); the residual partials of 33 x 44 CTAs are folded by the last."""
+    n = [1030, 700]
+    k = inputs.lognormal_k(n, seed=3, corr=4.0)
+    f = inputs.uniform_rhs(n, seed=9).ravel()
+    levels = [0, 1, 2, 3, 5]
+    u0 = np.zeros(f.size)
+    h, kt = make(S, n, S.SRJ_PREC_F64, k=k)
+    fd, ud = dev(f), dev(u0)
+    try:
+        rn = S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    P = orc.Problem(n, k=k)
+    uo, rno = orc.run_levels(P, f, u0, levels)
+    assert np.max(np.abs(ug - uo)) <= 1e-10 * np.max(np.abs(uo))
+    r0 = orc.residual_norm(P, u0, f)
+    assert np.all(np.abs(rn - rno) <= 1e-10 * rno + 1e-13 * r0)
+
+
 @pytest.mark.parametrize("name,n,eps,kind", CASES, ids=[c[0] for c in CASES])
 def test_heuristic_solve_f64(S, orc, name, n, eps, kind):
     """Whole solve with Alg. 1: identical level sequence and sweep count,
