@@ -192,6 +192,8 @@ PassLaunch make_launch(srj_handle *h, bool inner) {
 }
 
 // Graph: WHILE(cond) { pass kernel }.  Built once per handle.
+constexpr int kPassNodes = 4;  // generic pass nodes per iteration of the solve loop
+
 srj_status build_graph(srj_handle *h) {
     if (h->exec) return SRJ_OK;
     CK(cudaGraphCreate(&h->graph, 0));
@@ -213,6 +215,22 @@ srj_status build_graph(srj_handle *h) {
         CK(add_wave2d_node(h->wplan, a, body));
     } else {
         CK(add_generic_pass_node(h->kprec, h->vark, a, body, h->p3maps));
+        // one-sweep passes are short: chain copies of the pass node so that
+        // the conditional node is evaluated once per kPassNodes passes (a pass
+        // that starts after the end of the solve exits at once)
+        size_t nn = 0;
+        CK(cudaGraphGetNodes(body, nullptr, &nn));
+        if (nn == 1) {
+            cudaGraphNode_t prev;
+            CK(cudaGraphGetNodes(body, &prev, &nn));
+            cudaKernelNodeParams kp{};
+            CK(cudaGraphKernelNodeGetParams(prev, &kp));
+            for (int i = 1; i < kPassNodes; ++i) {
+                cudaGraphNode_t nd;
+                CK(cudaGraphAddKernelNode(&nd, body, &prev, 1, &kp));
+                prev = nd;
+            }
+        }
     }
     CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
     return SRJ_OK;
