@@ -37,6 +37,10 @@ TOL = 1e-8
 # low-part adds for t (40); then one two-product, one FMA, one two-sum, two
 # adds and one Dekker renormalisation (3) for u + omega t (14).
 DF_OPS_PER_LUP = 46  # FP32 instructions per update of the isotropic FP32-pair form (32 + df_axpy 14)
+# algorithmic HBM bytes of an FP32 sweep per grid point and pass: read u, read
+# f, write u (4 B each); 3D variable coefficients add k (4 B)
+ALGO_BYTES_PER_POINT = 12.0
+ALGO_BYTES_PER_POINT_VARK = 16.0
 WORKLOAD = ("2D Poisson 5-point, 4096x4096 interior, zero Dirichlet, f~U[-1,1] (seed 0+rank), "
             "u0=0, rel residual 1e-8, SRJ scheme family + Alg. 1 heuristic")
 
@@ -193,9 +197,19 @@ def replica_throughput(world, lups_local, ms_local):
 
 
 # ----------------------------------------------------------------- oracle arm
-def oracle_sample(seconds_budget=15.0):
+def host_cores():
+    """Host cores this process may run on (the OpenMP oracle's thread count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(seconds_budget=15.0, parallel=False):
     """Time the FP64 oracle's sweeps on the same 4096^2 problem: whole cycles
-    at levels 0, 1, 2, ... until the budget is used.  Returns (GLUP/s, text)."""
+    at levels 0, 1, 2, ... until the budget is used; parallel=True runs the
+    OpenMP build of the same source on all host cores.  Returns (GLUP/s,
+    seconds, text, threads)."""
     import numpy as np
 
     from oracle import oracle as O
@@ -204,18 +218,37 @@ def oracle_sample(seconds_budget=15.0):
     f = inputs.uniform_rhs(n, seed=0).ravel()
     P = O.Problem(n)
     u = np.zeros(f.size)
+    threads = 1
+    if parallel:
+        threads = int(os.environ.get("OMP_NUM_THREADS", host_cores()))
+        O.omp_lib()
     t0 = time.perf_counter()
     sweeps, level = 0, 0
     while True:
         w = O.level_omegas(level)
-        u = O.sweeps(P, u, f, w)
+        u = O.sweeps(P, u, f, w, parallel=parallel)
         sweeps += len(w)
         level += 1
         if time.perf_counter() - t0 > seconds_budget:
             break
     dt = time.perf_counter() - t0
-    return sweeps * f.size / dt / 1e9, dt, "%d sweeps (cycles at levels 0..%d) of the 4096^2 problem" % (
-        sweeps, level - 1)
+    text = "%d sweeps (cycles at levels 0..%d) of the 4096^2 problem, %d thread%s" % (
+        sweeps, level - 1, threads, "" if threads == 1 else "s")
+    return sweeps * f.size / dt / 1e9, dt, text, threads
+
+
+def cpu_baseline_line(seconds_all, seconds_one):
+    """The oracle on all host cores (the reported baseline) and on one core."""
+    try:
+        v, _, sample, threads = oracle_sample(seconds_all, parallel=True)
+    except (OSError, subprocess.CalledProcessError) as e:  # no OpenMP toolchain
+        v, _, sample, threads = oracle_sample(seconds_all)
+        sample += " (OpenMP build unavailable: %s)" % str(e).splitlines()[0][:80]
+    out = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+    if seconds_one > 0:
+        v1, _, s1, _ = oracle_sample(seconds_one)
+        out["single_core"] = {"value": v1, "unit": UNIT, "cores": 1, "sample": s1}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -224,11 +257,16 @@ def run_reference(args, rank, world):
     from oracle import oracle as O
     O.build()
     budget = float(os.environ.get("SRJ_ORACLE_STEP_SECONDS", "6"))
+    try:
+        O.build_omp()
+        parallel = True
+    except (OSError, subprocess.CalledProcessError):
+        parallel = False
     for _ in range(args.warmup):
-        oracle_sample(budget / 4)
-    vals, times, sample = [], [], ""
+        oracle_sample(budget / 4, parallel=parallel)
+    vals, times, sample, threads = [], [], "", 1
     for _ in range(args.steps):
-        v, dt, sample = oracle_sample(budget)
+        v, dt, sample, threads = oracle_sample(budget, parallel=parallel)
         vals.append(v)
         times.append(dt)
     value = statistics.median(vals)
@@ -238,7 +276,7 @@ def run_reference(args, rank, world):
         "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [SIDE, SIDE]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "each step: " + sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -456,10 +494,23 @@ def vark3d_leg(srj, inputs, torch, stream, seed=0, side=512, fp64=True):
                       "rel_residual": st["rn"] / st["r0"],
                       "status": srj.STATUS_NAMES[st["status"]]}
         if label == "mixed":
-            # one FP32-pair sweep moves 36 B per update: iterate hi/lo read and
-            # write (16), rhs (4), three face weights and 1/D (16)
-            res[label]["hbm_effective_frac"] = (36.0 * res[label]["glups"] /
-                                                peaks()[0])
+            # roofline of the inner pass (plane3d_kernel, one sweep per pass):
+            # algorithmic 16 B per update (read u, r, k; write u, FP32), over
+            # the device time of the inner cycle loops; the FP32-pair design
+            # moves 36 B (iterate hi/lo read and write 16, rhs 4, three face
+            # weights and 1/D 16)
+            hbm_peak, peak_kind = peaks()
+            inner_s = st["inner_seconds"]
+            ach = ALGO_BYTES_PER_POINT_VARK * st["sweeps"] * f.numel() / inner_s / 1e9
+            res[label]["inner_seconds"] = inner_s
+            res[label]["roofline"] = {
+                "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "kernel": "plane3d_kernel<FP32-pair, variable k>",
+                "algorithmic_bytes_per_update": ALGO_BYTES_PER_POINT_VARK,
+                "bytes_moved_per_update_by_design": 36.0,
+                "design_bytes_frac": 36.0 * st["sweeps"] * f.numel() / inner_s / 1e9 / hbm_peak,
+                "timing": "CUDA events around the inner cycle loops",
+                "peak_kind": peak_kind}
         sols[label] = u
     if "plain_fp64" in sols:
         d = torch.linalg.norm(sols["mixed"] - sols["plain_fp64"]) / torch.linalg.norm(
@@ -523,18 +574,24 @@ def run_ours(args, rank, world):
     Au = hinv2 * (4 * uu - up[1:-1, :-2] - up[1:-1, 2:] - up[:-2, 1:-1] - up[2:, 1:-1])
     rel_check = float(torch.linalg.norm(ff - Au) / torch.linalg.norm(ff))
 
-    # dominant kernel: the inner pass.  Its per-launch time is taken as the
-    # timed device time divided by the passes (an upper bound: it includes the
-    # few outer FP64 kernels and the loop-node overhead between passes).
+    # dominant kernel: the inner pass.  Its average launch duration is the
+    # device time of the cycle loops (CUDA events around each inner solve's
+    # loop on the library's stream, so without the outer FP64 kernels) over
+    # the passes they ran.
     clocks = clk.summary()
-    pass_ms = ms / max(passes, 1)
+    inner_s = sum(s["inner_seconds"] for s in stats)
+    pass_s = inner_s / max(passes, 1)
     sweeps_per_pass = sweeps / max(passes, 1)
-    bytes_per_pass = 20.0 * npts  # FP32-pair iterate read+write (8+8) + FP32 rhs (4)
     hbm_peak, peak_kind = peaks()
-    hbm_achieved = bytes_per_pass / (pass_ms * 1e-3) / 1e9
+    # algorithmic bytes of the FP32 inner sweep: read u, read f, write u,
+    # 4 B each per grid point and HBM pass; effective: per update
+    algo_per_pass = ALGO_BYTES_PER_POINT * npts
+    hbm_achieved = algo_per_pass / pass_s / 1e9
+    hbm_effective = ALGO_BYTES_PER_POINT * sweeps * npts / inner_s / 1e9
+    moved_per_pass = 20.0 * npts  # what the FP32-pair design moves: hi, lo read+write, rhs
     sm_mhz = clocks["sm_mhz"] or 2070.0
     alu_peak = fp32_issue_peak(sm_mhz)
-    alu_achieved = DF_OPS_PER_LUP * npts * sweeps_per_pass / (pass_ms * 1e-3) / 1e12
+    alu_achieved = DF_OPS_PER_LUP * npts * sweeps_per_pass / pass_s / 1e12
 
     # end to end through srj_solve_host with pinned host buffers
     e2e_val = None
@@ -613,14 +670,14 @@ def run_ours(args, rank, world):
     if not args.no_paper:
         studies = paper_studies_leg(srj, inputs, torch, stream, seed=rank)
     vark = None
-    if args.with_3d:
+    if not args.no_3d:
         vark = vark3d_leg(srj, inputs, torch, stream, seed=rank, side=args.side3d,
                           fp64=not args.no_fp64)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, sample = oracle_sample(float(os.environ.get("SRJ_ORACLE_SECONDS", "15")))
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = cpu_baseline_line(float(os.environ.get("SRJ_ORACLE_SECONDS", "12")),
+                                float(os.environ.get("SRJ_ORACLE_SECONDS_1CORE", "8")))
 
     if rank == 0:
         line = {
@@ -637,22 +694,25 @@ def run_ours(args, rank, world):
             "time_to_tol_s": ms_max / args.steps / 1e3,
             "sweeps_per_solve": sweeps / args.steps, "outer_per_solve": outer / args.steps,
             "converged": ok, "rel_residual_check": rel_check,
-            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
-                         "unit": "T FP32-instr/s", "frac": alu_achieved / alu_peak,
+            "roofline": {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                          "traffic": profiled_traffic(),
-                         "kernel": "wave2d_kernel<FP32-pair> inner pass, %d ops/LUP, "
-                                   "%.2f sweeps/pass; per-pass time = timed device time / passes"
-                                   % (DF_OPS_PER_LUP, sweeps_per_pass),
-                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x median SM clock "
-                                      "%.0f MHz" % sm_mhz},
-            "roofline_hbm": {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak,
-                             "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
-                             "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                             "bytes_per_pass": bytes_per_pass,
-                             # counting temporal blocking: the bytes one sweep per
-                             # pass would move (20 B per update) at the achieved rate
-                             "effective_frac": 20.0 * npts * sweeps_per_pass / (pass_ms * 1e-3)
-                             / 1e9 / hbm_peak},
+                         "effective_achieved": hbm_effective,
+                         "effective_frac": hbm_effective / hbm_peak,
+                         "algorithmic_bytes_per_launch": algo_per_pass,
+                         "bytes_moved_per_launch_by_design": moved_per_pass,
+                         "sweeps_per_launch": sweeps_per_pass,
+                         "launch_us": pass_s * 1e6,
+                         "kernel": "wave2d_kernel<FP32-pair> inner pass; algorithmic 12 B per "
+                                   "point per pass (read u, f; write u, FP32); effective_* "
+                                   "counts the %.2f fused sweeps of a pass" % sweeps_per_pass,
+                         "timing": "CUDA events around the inner cycle loops / passes",
+                         "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy burst)"},
+            "roofline_issue": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                               "unit": "T FP32-instr/s", "frac": alu_achieved / alu_peak,
+                               "ops_per_update": DF_OPS_PER_LUP,
+                               "peak_kind": "derived: 152 SMs x 128 FP32 lanes x median SM "
+                                            "clock %.0f MHz" % sm_mhz},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * npts,
                     "d2h_bytes_per_step": 8 * npts},
             "gpu_launches": int(passes + 2 * outer + args.steps),
@@ -686,7 +746,8 @@ def main():
     ap.add_argument("--no-mg", action="store_true", help="skip the multigrid leg")
     ap.add_argument("--no-paper", action="store_true",
                     help="skip the Sec. 4.1 / Sec. 4.2.2 studies")
-    ap.add_argument("--with-3d", action="store_true", help="add the 3D variable-k leg")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D variable-k leg")
+    ap.add_argument("--with-3d", action="store_true", help=argparse.SUPPRESS)  # the default now
     ap.add_argument("--side3d", type=int, default=512)
     ap.add_argument("--f32-depth", type=int, default=0, help="temporal depth of the FP32 leg")
     ap.add_argument("--depth", type=int, default=0, help="temporal depth of the inner pass (0: library)")

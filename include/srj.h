@@ -54,7 +54,7 @@ typedef enum srj_status {
     SRJ_ECUDA = 3,        /* a CUDA runtime call failed (see srj_last_error) */
     SRJ_ENOTCONV = 4,     /* sweep cap reached before the tolerance */
     SRJ_EDIVERGED = 5,    /* the residual norm became non-finite */
-    SRJ_ETIMEOUT = 6,     /* reserved: a bounded device-side wait expired */
+    SRJ_ETIMEOUT = 6,     /* a bounded device-side wait expired (srj_set_wait_limit) */
     SRJ_EUNSUPPORTED = 7  /* valid request the library does not implement */
 } srj_status;
 
@@ -151,6 +151,10 @@ typedef struct srj_stats {
     double r0;           /* ||f - A u0||_2 */
     double rn;           /* ||f - A u||_2 at exit (FP64 for F64 and MIXED) */
     double seconds;      /* device time of the solve, CUDA events */
+    double inner_seconds; /* device time of the cycle loop alone (the sweep
+                             passes with their fused norms and selection;
+                             for MIXED summed over the inner solves, without
+                             the FP64 outer kernels), CUDA events */
 } srj_stats;
 
 /* Library version string (static storage). */
@@ -272,20 +276,23 @@ srj_status srj_mlp_train(const float *x_dev, const int32_t *y_dev, int64_t n,
  * allocating any memory, for callers that cannot call cudaMalloc or cudaFree:
  * code running under a device-memory pool or budget it does not own, or on a
  * path where cudaFree's device-wide synchronisation is unacceptable.  The
- * paper has no counterpart; this is a deployment variant of the residual
- * reduction that drives Alg. 1.
+ * paper has no counterpart.
  *
  * Its reduction scratch is a fixed device array inside the library (one
  * partial sum per grid row plus a counter, about 512 KB, held by every GPU
  * that loads the library until the process exits), so grids with more than
- * 65536 rows (n1 * n2 > 65536) are rejected with SRJ_EINVAL; variable
- * coefficients (stencil->k != NULL) and Neumann axes give SRJ_EUNSUPPORTED.  The first call on
- * a device looks up that array's device address (cudaGetSymbolAddress with
- * the device current) and caches it; make that first call before any stream
- * capture.  Every call clears the counter it needs; all calls on a device
- * share the array, so calls whose work overlaps on the GPU (other streams or
- * host threads) race and must be serialised by the caller.  Work is queued on
- * `stream` (NULL = legacy default) and synchronised before returning. */
+ * 65536 rows (n1 * n2 > 65536) are rejected with SRJ_EINVAL, as are a
+ * negative or non-finite spacing h[a] or coefficient eps[a] (0 selects the
+ * default, as in srj_create); variable coefficients (stencil->k or a_diag
+ * set) and Neumann axes give SRJ_EUNSUPPORTED.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress with the device
+ * current) and caches it; make that first call before any stream capture.
+ * The cached address does not survive cudaDeviceReset: do not call this
+ * function on a device after resetting it.  Every call clears the counter it
+ * needs; all calls on a device share the array, so calls whose work overlaps
+ * on the GPU (other streams or host threads) race and must be serialised by
+ * the caller.  Work is queued on `stream` (NULL = legacy default), and the
+ * call synchronises `stream` before it returns the norm in *out. */
 srj_status srj_residual_norm_noalloc(const srj_grid *grid, const srj_stencil *stencil,
                                      const double *f, const double *u, double *out,
                                      void *stream);
@@ -321,6 +328,20 @@ srj_status srj_mg_create(const srj_grid *grid, const srj_stencil *stencil,
  * The handle must come from srj_mg_create (SRJ_EINVAL otherwise). */
 srj_status srj_mg_solve(srj_handle *h, const double *f, double *u, double tol,
                         srj_stats *stats);
+
+/* Failure detection (the paper has no counterpart): the 3D pass waits for
+ * every plane it stages in shared memory at most `polls` polls of its
+ * mbarrier (default 4194304; a negative value restores the default, 0 makes
+ * the first wait give up at once).  A wait that runs out ends the solve with
+ * SRJ_ETIMEOUT instead of hanging: the pass still waits, with the default
+ * limit, for the copies it has in flight, takes part in the pass's
+ * bookkeeping and returns; later passes of the solve exit at once.  After
+ * SRJ_ETIMEOUT the contents of u are unspecified; the handle stays usable and
+ * the next solve starts from a clean state.  A timeout at the default limit
+ * means the copies did not complete: check the CUDA context
+ * (cudaDeviceSynchronize) and destroy the handle.  Takes effect from the
+ * next solve on h.  Other kernels have no device-side waits. */
+srj_status srj_set_wait_limit(srj_handle *h, int64_t polls);
 
 /* Text describing the last failure on h (static storage inside h), or a
  * generic text for h == NULL. */

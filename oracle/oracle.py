@@ -26,18 +26,34 @@ _lib = None
 MAX_LEVEL = 24
 
 
+_OMP_PATH = os.path.join(_BUILD, "libsrj_oracle_omp.so")
+_lib_omp = None
+
+
+def _compile(out, extra):
+    with _lock:
+        stale = (not os.path.exists(out)) or (os.path.getmtime(out) < os.path.getmtime(_SRC))
+        if stale:
+            os.makedirs(_BUILD, exist_ok=True)
+            tmp = out + ".%d.tmp" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
+                                   "-D_DEFAULT_SOURCE"] + extra + ["-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/libsrj_oracle.so``."""
-    with _lock:
-        stale = (not os.path.exists(_LIB_PATH)) or (
-            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
-        if force or stale:
-            os.makedirs(_BUILD, exist_ok=True)
-            tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
-                                   "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
-            os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    if force and os.path.exists(_LIB_PATH):
+        os.unlink(_LIB_PATH)
+    return _compile(_LIB_PATH, [])
+
+
+def build_omp() -> str:
+    """The same source compiled with ``-fopenmp`` (only the sweep's row loop
+    carries a pragma; every result is the same as the plain build's).  Used
+    to time the CPU baseline on all host cores."""
+    return _compile(_OMP_PATH, ["-fopenmp"])
 
 
 class _Problem(C.Structure):
@@ -49,46 +65,59 @@ class _Problem(C.Structure):
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
-        dp = C.POINTER(C.c_double)
-        ip = C.POINTER(C.c_int)
-        lp = C.POINTER(C.c_long)
-        pp = C.POINTER(_Problem)
-        L.oracle_level_m.argtypes = [C.c_int]
-        L.oracle_level_m.restype = C.c_int
-        L.oracle_lambda_star.argtypes = [C.c_int]
-        L.oracle_lambda_star.restype = C.c_double
-        L.oracle_scheme_root_order.argtypes = [C.c_int, dp, dp]
-        L.oracle_leja_order.argtypes = [C.c_int, dp, ip]
-        L.oracle_level_omegas.argtypes = [C.c_int, dp]
-        L.oracle_level_omegas.restype = C.c_int
-        L.oracle_amplification.argtypes = [C.c_int, dp, C.c_double]
-        L.oracle_amplification.restype = C.c_double
-        L.oracle_apply_A.argtypes = [pp, dp, dp]
-        L.oracle_diagonal.argtypes = [pp, dp]
-        L.oracle_residual_norm.argtypes = [pp, dp, dp]
-        L.oracle_residual_norm.restype = C.c_double
-        L.oracle_sweep.argtypes = [pp, dp, dp, C.c_double, dp]
-        L.oracle_sweeps.argtypes = [pp, dp, dp, dp, C.c_long]
-        L.oracle_next_level.argtypes = [C.c_int, C.c_double, C.c_int]
-        L.oracle_next_level.restype = C.c_int
-        L.oracle_srj_solve.argtypes = [pp, dp, dp, C.c_double, C.c_int, C.c_int,
-                                       C.c_int, C.c_long, lp, lp, dp, dp, ip,
-                                       dp, C.c_long]
-        L.oracle_srj_solve.restype = C.c_int
-        L.oracle_srj_run_levels.argtypes = [pp, dp, dp, ip, C.c_long, dp]
-        L.oracle_jacobi_solve.argtypes = [pp, dp, dp, C.c_double, C.c_int,
-                                          C.c_long, C.c_long, lp, dp]
-        L.oracle_jacobi_solve.restype = C.c_int
-        L.oracle_thomas.argtypes = [C.c_long, dp, dp, dp, dp, dp]
-        L.oracle_mg_restrict.argtypes = [pp, dp, pp, dp]
-        L.oracle_mg_prolong_add.argtypes = [pp, dp, pp, dp]
-        L.oracle_mg_vcycle.argtypes = [pp, dp, dp, C.c_int, C.c_int, C.c_int]
-        L.oracle_mg_solve.argtypes = [pp, dp, dp, C.c_double, C.c_int, C.c_int, C.c_int,
-                                      C.c_long, lp, dp, dp, dp]
-        L.oracle_mg_solve.restype = C.c_int
-        _lib = L
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def omp_lib():
+    """The OpenMP build (see build_omp); its thread count follows
+    OMP_NUM_THREADS, default all host cores."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _declare(C.CDLL(build_omp()))
+    return _lib_omp
+
+
+def _declare(L):
+    """Argument and result types of the oracle's C functions."""
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int)
+    lp = C.POINTER(C.c_long)
+    pp = C.POINTER(_Problem)
+    L.oracle_level_m.argtypes = [C.c_int]
+    L.oracle_level_m.restype = C.c_int
+    L.oracle_lambda_star.argtypes = [C.c_int]
+    L.oracle_lambda_star.restype = C.c_double
+    L.oracle_scheme_root_order.argtypes = [C.c_int, dp, dp]
+    L.oracle_leja_order.argtypes = [C.c_int, dp, ip]
+    L.oracle_level_omegas.argtypes = [C.c_int, dp]
+    L.oracle_level_omegas.restype = C.c_int
+    L.oracle_amplification.argtypes = [C.c_int, dp, C.c_double]
+    L.oracle_amplification.restype = C.c_double
+    L.oracle_apply_A.argtypes = [pp, dp, dp]
+    L.oracle_diagonal.argtypes = [pp, dp]
+    L.oracle_residual_norm.argtypes = [pp, dp, dp]
+    L.oracle_residual_norm.restype = C.c_double
+    L.oracle_sweep.argtypes = [pp, dp, dp, C.c_double, dp]
+    L.oracle_sweeps.argtypes = [pp, dp, dp, dp, C.c_long]
+    L.oracle_next_level.argtypes = [C.c_int, C.c_double, C.c_int]
+    L.oracle_next_level.restype = C.c_int
+    L.oracle_srj_solve.argtypes = [pp, dp, dp, C.c_double, C.c_int, C.c_int,
+                                   C.c_int, C.c_long, lp, lp, dp, dp, ip,
+                                   dp, C.c_long]
+    L.oracle_srj_solve.restype = C.c_int
+    L.oracle_srj_run_levels.argtypes = [pp, dp, dp, ip, C.c_long, dp]
+    L.oracle_jacobi_solve.argtypes = [pp, dp, dp, C.c_double, C.c_int,
+                                      C.c_long, C.c_long, lp, dp]
+    L.oracle_jacobi_solve.restype = C.c_int
+    L.oracle_thomas.argtypes = [C.c_long, dp, dp, dp, dp, dp]
+    L.oracle_mg_restrict.argtypes = [pp, dp, pp, dp]
+    L.oracle_mg_prolong_add.argtypes = [pp, dp, pp, dp]
+    L.oracle_mg_vcycle.argtypes = [pp, dp, dp, C.c_int, C.c_int, C.c_int]
+    L.oracle_mg_solve.argtypes = [pp, dp, dp, C.c_double, C.c_int, C.c_int, C.c_int,
+                                  C.c_long, lp, dp, dp, dp]
+    L.oracle_mg_solve.restype = C.c_int
+    return L
 
 
 def _dp(a):
@@ -207,11 +236,13 @@ def sweep(P: Problem, u, f, omega: float):
     return out
 
 
-def sweeps(P: Problem, u, f, omegas):
+def sweeps(P: Problem, u, f, omegas, parallel=False):
+    """Apply the factors in order.  parallel=True runs the OpenMP build
+    (same arithmetic, rows shared among the host threads)."""
     u = _f64(u).ravel().copy()
     f = _f64(f).ravel()
     w = _f64(omegas)
-    lib().oracle_sweeps(P._c(), _dp(u), _dp(f), _dp(w), len(w))
+    (omp_lib() if parallel else lib()).oracle_sweeps(P._c(), _dp(u), _dp(f), _dp(w), len(w))
     return u
 
 

@@ -71,6 +71,8 @@ struct srj_handle {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evl0 = nullptr, evl1 = nullptr;  // around the cycle loop
+    long long wait_limit = kDefaultWaitLimit;     // srj_set_wait_limit
     long long last_cycles = 0;
     std::string err;
     struct BatchData *batch = nullptr;  // srj_create_batched handles only
@@ -264,6 +266,22 @@ srj_status run_loop(srj_handle *h) {
     }
 }
 
+// run_loop bracketed by the loop events; loop_ms() reads their interval once
+// the stream has passed the second one.
+srj_status run_loop_timed(srj_handle *h) {
+    CK(cudaEventRecord(h->evl0, h->stream));
+    const srj_status s = run_loop(h);
+    if (s != SRJ_OK) return s;
+    CK(cudaEventRecord(h->evl1, h->stream));
+    return SRJ_OK;
+}
+
+double loop_seconds(srj_handle *h) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->evl0, h->evl1) != cudaSuccess) return 0.0;
+    return ms * 1e-3;
+}
+
 void init_state(srj_handle *h, DevState &s, double tol, int tol_kind, int selector,
                 int level0, long long max_sweeps, int stall_stop, int nsched, int trace_base) {
     std::memset(&s, 0, sizeof(s));
@@ -280,6 +298,7 @@ void init_state(srj_handle *h, DevState &s, double tol, int tol_kind, int select
     s.status = DST_RUNNING;
     s.dim = h->geo.dim;
     s.npoints = (double)h->npts;
+    s.wait_limit = h->wait_limit;
 }
 
 srj_status status_of(int dst) {
@@ -307,7 +326,7 @@ srj_status solve_plain(srj_handle *h, const void *f, void *u, double tol, int se
     init_state(h, *h->h_st, tol, h->opts.tol_kind, selector, level0, h->opts.max_sweeps, 0,
                nsched, 0);
     CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
-    s = run_loop(h);
+    s = run_loop_timed(h);
     if (s != SRJ_OK) return s;
     void *pads[2] = {h->U[0], h->U[1]};
     CK(copy_out_launch(h->kprec, h->geo, h->st, pads, u, st));
@@ -316,6 +335,7 @@ srj_status solve_plain(srj_handle *h, const void *f, void *u, double tol, int se
     const DevState &r = *h->h_st;
     h->last_cycles = r.cycles;
     if (stats) {
+        stats->inner_seconds = loop_seconds(h);
         stats->status = status_of(r.status);
         stats->final_level = r.level;
         stats->sweeps = r.sweeps;
@@ -373,6 +393,7 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
     int level = h->opts.level0, final_level = level;
     int result = DST_NOTCONV;
     int trace_base = 0;
+    double inner_s = 0.0;
     const size_t ebytes = (size_t)h->padded * sizeof(float);
     for (;;) {
         CK(outer_residual_launch(oa, st));
@@ -380,14 +401,15 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
         CK(cudaStreamSynchronize(st));
         if (outer > 0) {  // fold in the inner solve that just finished
             const DevState &r = *h->h_st;
+            inner_s += loop_seconds(h);
             sweeps += r.sweeps;
             cycles += r.cycles;
             passes += r.passes;
             final_level = r.level;
             level = r.level - kInnerCarry > 0 ? r.level - kInnerCarry : 0;
             trace_base += (int)r.cycles;
-            if (r.status == DST_DIVERGED) {
-                result = DST_DIVERGED;
+            if (r.status == DST_DIVERGED || r.status == DST_TIMEOUT) {
+                result = r.status;
                 break;
             }
         }
@@ -419,7 +441,7 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
         init_state(h, *h->h_st, eta, SRJ_TOL_REL, h->opts.selector, level, inner_cap, 1, 0,
                    trace_base);
         CK(cudaMemcpyAsync(h->st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
-        s = run_loop(h);
+        s = run_loop_timed(h);
         if (s != SRJ_OK) return s;
         CK(outer_update_launch(oa, st));
         CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
@@ -435,6 +457,7 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
         stats->passes = passes;
         stats->r0 = r0;
         stats->rn = rn;
+        stats->inner_seconds = inner_s;
     }
     return status_of(result);
 }
@@ -851,6 +874,8 @@ srj_status srj_create(const srj_grid *grid, const srj_stencil *stencil, const sr
     }
     ck(cudaEventCreate(&h->ev0), "event");
     ck(cudaEventCreate(&h->ev1), "event");
+    ck(cudaEventCreate(&h->evl0), "event");
+    ck(cudaEventCreate(&h->evl1), "event");
     ck(cudaStreamSynchronize(s), "create sync");
     if (rc != SRJ_OK) {
         srj_destroy(h);
@@ -1121,6 +1146,12 @@ srj_status srj_solve_batched(srj_handle *h, const double *const *f, double *cons
     return worst;
 }
 
+srj_status srj_set_wait_limit(srj_handle *h, int64_t polls) {
+    if (!h) return SRJ_EINVAL;
+    h->wait_limit = polls < 0 ? kDefaultWaitLimit : (long long)polls;
+    return SRJ_OK;
+}
+
 srj_status srj_mlp_set_weights(srj_handle *h, const uint16_t *w, int64_t count) {
     if (!h) return SRJ_EINVAL;
     if (h->mg) return fail(h, SRJ_EINVAL, "srj_mlp_set_weights: multigrid handle");
@@ -1386,6 +1417,8 @@ srj_status srj_destroy(srj_handle *h) {
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->evl0) cudaEventDestroy(h->evl0);
+    if (h->evl1) cudaEventDestroy(h->evl1);
     for (void *p : {(void *)h->w64, (void *)h->w32, h->F, h->U[0], h->U[1], h->Ulo[0], h->Ulo[1],
                     (void *)h->wx64, (void *)h->wy64, (void *)h->wz64, (void *)h->invd64,
                     (void *)h->wx32, (void *)h->wy32, (void *)h->wz32, (void *)h->invd32,

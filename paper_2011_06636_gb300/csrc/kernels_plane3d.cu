@@ -29,7 +29,6 @@ constexpr int kHX = 4;              // columns staged left of the tile: x0 - 4 i
 constexpr int kSX = kTX + 2 * kHX;  // staged row width: x0 - 4 .. x0 + 35
 constexpr int kPD = 3;              // planes in flight ahead of the one computed
 constexpr int kNS = kPD + 2;        // ring slots: planes z-1 .. z+PD
-constexpr long long kWaitLimit = 1LL << 22;  // bounded mbarrier wait (iterations)
 
 __host__ __device__ constexpr int al128(int b) { return (b + 127) / 128 * 128; }
 
@@ -62,11 +61,11 @@ __device__ __forceinline__ void bar_expect(uint64_t *bar, unsigned bytes) {
                  "r"(bytes)
                  : "memory");
 }
-// true once the phase with the given parity has completed; false after the
-// iteration limit
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity) {
+// true once the phase with the given parity has completed; false after
+// `limit` polls (at once for limit 0)
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, unsigned parity, long long limit) {
     const unsigned a = smem_u32(bar);
-    for (long long it = 0; it < kWaitLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -99,12 +98,14 @@ __global__ void __launch_bounds__(kTX * kTY)
     __shared__ __align__(8) uint64_t s_bar[kNS];
     __shared__ PassPlan s_plan;
     __shared__ double s_omega;
+    __shared__ long long s_wlim;
     __shared__ int s_err;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kTX * ty;
     if (tid == 0) {
         s_plan = plan_pass(a, 1);
         s_omega = (s_plan.run && s_plan.nsw) ? a.w64[s_plan.woff] : 0.0;
+        s_wlim = a.st->wait_limit;
         s_err = 0;
         if (!s_plan.run && a.cfg.use_cond && blockIdx.x == 0 && blockIdx.y == 0 &&
             blockIdx.z == 0)
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(kTX * kTY)
     const PassPlan p = s_plan;
     if (!p.run) return;
     const double omega = s_omega;
+    const long long wlim = s_wlim;
 
     const GridGeo &g = a.geo;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -146,8 +148,8 @@ __global__ void __launch_bounds__(kTX * kTY)
             tma3(s + L::o_id, &maps.invd, x0, y0, zz, bar);
         }
     };
-    auto wait = [&](int zz) -> bool {
-        return bar_wait(&s_bar[rel(zz) % kNS], (unsigned)((rel(zz) / kNS) & 1));
+    auto wait = [&](int zz, long long limit) -> bool {
+        return bar_wait(&s_bar[rel(zz) % kNS], (unsigned)((rel(zz) / kNS) & 1), limit);
     };
     auto ld = [&](const unsigned char *s, int off, int idx) -> C {
         return *(const C *)(s + off + idx * ES);
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kTX * kTY)
     double part = 0.0;  // residual sum (resid pass)
     long long dbits = 0;  // largest |u' - u| of the sweep (abs_diff_bits)
     int last_issued = z0 + kPD - 1;  // planes issued so far: z0 - 1 .. last_issued
-    int next_wait = z0 - 1;          // first plane not yet waited for
+    int next_wait = z0 - 1;          // first plane this thread has not seen land
     bool ok = true;
     // ring slots of planes z - 1, z, z + 1 (advanced with z, no modulo)
     int im = 0, i0 = 1 % kNS, ip = 2 % kNS;
@@ -183,7 +185,12 @@ __global__ void __launch_bounds__(kTX * kTY)
     T u_m = zero_u<PREC>(), u_c = zero_u<PREC>();
     C wz_m = C(0);
     for (int z = z0; z < z1; ++z) {
-        for (; next_wait <= z + 1; ++next_wait) ok = ok && wait(next_wait);
+        // a wait that runs out leaves next_wait at its plane, so the drain
+        // below waits for that plane and every later one
+        while (ok && next_wait <= z + 1) {
+            if (wait(next_wait, wlim)) ++next_wait;
+            else ok = false;
+        }
         // one decision for the whole block (a bounded wait may run out in one
         // thread and not in another); the barrier also means every thread is
         // done with plane z - 2's slot
@@ -241,9 +248,11 @@ __global__ void __launch_bounds__(kTX * kTY)
         i0 = ip;
         ip = ip + 1 == kNS ? 0 : ip + 1;
     }
-    // copies still in flight land before the CTA's shared memory goes away
-    // (each wait is bounded); a wait that ran out marks the solve
-    for (; next_wait <= last_issued; ++next_wait) ok = wait(next_wait) && ok;
+    // every copy still in flight lands before the CTA's shared memory goes
+    // away: after a wait that ran out too (this drain uses the default limit,
+    // so a solve with a short limit still exits cleanly); a wait that ran out
+    // marks the solve
+    for (; next_wait <= last_issued; ++next_wait) ok = wait(next_wait, kDefaultWaitLimit) && ok;
     if (!ok) atomicOr(&s_err, 1);
     __syncthreads();
     if (s_err && tid == 0) atomicExch(&a.st->status, (int)DST_TIMEOUT);

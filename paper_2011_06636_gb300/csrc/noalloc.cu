@@ -12,7 +12,9 @@
 // (about 512 KB) until the process exits.  Host code cannot use the array's
 // name as a device address, so the first call on each device looks the
 // address up with cudaGetSymbolAddress (with that device current) and caches
-// it; later calls on that device reuse it.
+// it; later calls on that device reuse it.  A cudaDeviceReset tears down the
+// module that holds the array, so the cached address is not valid across a
+// reset: this entry point must not be used after the device was reset.
 //
 // All calls on a device share the one array: the counter is cleared at the
 // start of each call, and calls whose kernels overlap on the GPU (different
@@ -103,10 +105,15 @@ extern "C" srj_status srj_residual_norm_noalloc(const srj_grid *grid, const srj_
     long long n[3] = {1, 1, 1};
     double c[3] = {0, 0, 0};
     for (int a = 0; a < grid->dim; ++a) {
+        // the same argument checks as srj_create: a negative or non-finite
+        // spacing or coefficient is an error, zero means the default
         if (grid->n[a] < 1 || grid->n[a] > (1LL << 30)) return SRJ_EINVAL;
+        if (grid->h[a] < 0 || !std::isfinite(grid->h[a])) return SRJ_EINVAL;
+        const double ea = stencil ? stencil->eps[a] : 0.0;
+        if (ea < 0 || !std::isfinite(ea)) return SRJ_EINVAL;
         n[a] = grid->n[a];
         const double h = grid->h[a] > 0 ? grid->h[a] : 1.0 / (double)(n[a] + 1);
-        const double e = (stencil && stencil->eps[a] > 0) ? stencil->eps[a] : 1.0;
+        const double e = ea > 0 ? ea : 1.0;
         c[a] = e / (h * h);
     }
     if (n[1] * n[2] > kNaMaxRows) return SRJ_EINVAL;  // beyond the scratch: ny * nz > 65536

@@ -23,6 +23,10 @@ constexpr int kMaxLevel = 24;
 // inner solve was working on, so restarting lower only repeats the climb).
 constexpr int kInnerCarry = 0;
 constexpr int kNumLevels = 25;
+// Polls of a bounded device-side wait (the 3D pass waiting for a staged plane)
+// before it gives up and ends the solve with SRJ_ETIMEOUT; copies in flight
+// are then still drained with this limit.
+constexpr long long kDefaultWaitLimit = 1LL << 22;
 constexpr int kTotalOmegas = 9710;  // sum of M over the 25 levels
 
 // App. B table (scheme level -> M) and the offset of each level's factors in
@@ -68,6 +72,7 @@ struct DevState {
     int32_t max_level;
     int32_t stall_stop;   // 1: stop when a cycle's ratio >= 1 (inner of MIXED)
     int32_t nsched;       // DSEL_SCHEDULE: number of scheduled cycles
+    long long wait_limit; // polls a bounded device-side wait makes before it gives up
     // running state
     int32_t level;        // level of the cycle in progress
     int32_t k;            // sweeps of the current cycle already done

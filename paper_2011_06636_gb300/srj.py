@@ -27,7 +27,7 @@ EXPORTS = ["srj_version", "srj_level_m", "srj_scheme_omegas", "srj_create", "srj
            "srj_solve_host", "srj_run_levels", "srj_residual_norm", "srj_get_trace",
            "srj_create_batched", "srj_solve_batched", "srj_mlp_set_weights", "srj_mlp_forward",
            "srj_mlp_train", "srj_residual_norm_noalloc", "srj_mg_create", "srj_mg_solve",
-           "srj_last_error", "srj_destroy"]
+           "srj_set_wait_limit", "srj_last_error", "srj_destroy"]
 
 
 class srj_grid(C.Structure):
@@ -55,7 +55,8 @@ class srj_mg_opts(C.Structure):
 class srj_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("final_level", C.c_int32), ("sweeps", C.c_int64),
                 ("cycles", C.c_int64), ("outer", C.c_int64), ("passes", C.c_int64),
-                ("r0", C.c_double), ("rn", C.c_double), ("seconds", C.c_double)]
+                ("r0", C.c_double), ("rn", C.c_double), ("seconds", C.c_double),
+                ("inner_seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,6 +120,8 @@ def load(build_if_missing: bool = True):
     L.srj_mg_create.restype = C.c_int
     L.srj_mg_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(srj_stats)]
     L.srj_mg_solve.restype = C.c_int
+    L.srj_set_wait_limit.argtypes = [H, C.c_int64]
+    L.srj_set_wait_limit.restype = C.c_int
     L.srj_destroy.argtypes = [H]
     L.srj_destroy.restype = C.c_int
     _lib = L
@@ -301,6 +304,14 @@ def srj_mlp_train(x_ptr, y_ptr, n, order_ptr, steps, batch, lr, theta_ptr, strea
     if rc != SRJ_OK:
         raise SrjError(rc, "srj_mlp_train")
     return loss[:steps]
+
+
+def srj_set_wait_limit(h, polls):
+    """Polls a bounded device-side wait makes before the solve ends with
+    SRJ_ETIMEOUT (negative: the library default)."""
+    rc = load().srj_set_wait_limit(h, int(polls))
+    if rc != SRJ_OK:
+        raise SrjError(rc, "srj_set_wait_limit")
 
 
 def srj_last_error(h) -> str:

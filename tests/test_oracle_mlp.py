@@ -95,3 +95,63 @@ def test_features():
     assert x[8] == pytest.approx(math.log10(4096 ** 2) / 10)
     assert x[9] == pytest.approx(2 / 3) and x[10] == 1.0 and x[11] == pytest.approx(1.0)
     assert M.features([1e-30], 10, 1, 0)[0] == -20.0
+
+
+def _theta_with_logits(z):
+    """Parameters whose network returns the logits z for every input: all
+    weights zero, the last bias set to z (the hidden layers output zeros)."""
+    th = np.zeros(M.N_PARAMS)
+    th[-M.N_OUT:] = z
+    return th
+
+
+def test_decide_moves_clamps_and_ties():
+    """The selector's move rule: argmax of the logits over {L-1, L, L+1}
+    inside [0, 24], ties to the lower level.  Each case fails a plausible
+    slip: a global argmax, ties to the higher level, no clamp at either end."""
+    x = np.zeros(12)
+    # global maximum far away: only the three neighbouring levels count
+    z = np.zeros(25)
+    z[20] = 9.0
+    z[6] = 1.0
+    assert M.decide(_theta_with_logits(z), x, 5) == 6
+    z = np.zeros(25)
+    z[0] = 9.0
+    z[4] = 1.0
+    assert M.decide(_theta_with_logits(z), x, 5) == 4
+    # all equal: the lowest of the three moves
+    assert M.decide(_theta_with_logits(np.zeros(25)), x, 5) == 4
+    # a tie between two moves above a third: the lower of the two
+    z = np.zeros(25)
+    z[5] = z[6] = 2.0
+    assert M.decide(_theta_with_logits(z), x, 5) == 5
+    z = np.zeros(25)
+    z[4] = z[6] = 2.0
+    assert M.decide(_theta_with_logits(z), x, 5) == 4
+    # level 0 cannot decrease; with equal logits it stays
+    assert M.decide(_theta_with_logits(np.zeros(25)), x, 0) == 0
+    z = np.zeros(25)
+    z[1] = 1.0
+    assert M.decide(_theta_with_logits(z), x, 0) == 1
+    # the top level cannot increase, even when its own logit loses
+    z = np.zeros(25)
+    z[23] = 1.0
+    assert M.decide(_theta_with_logits(z), x, 24) == 23
+    assert M.decide(_theta_with_logits(np.zeros(25)), x, 24) == 23
+    z = np.zeros(25)
+    z[24] = 1.0
+    assert M.decide(_theta_with_logits(z), x, 24) == 24
+    # a lowered top clamps the move set too
+    z = np.zeros(25)
+    z[11] = 5.0
+    z[10] = 1.0
+    assert M.decide(_theta_with_logits(z), x, 10, top=10) == 10
+    # every decision is one of the allowed moves, on random logits
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        z = rng.standard_normal(25)
+        L = int(rng.integers(0, 25))
+        got = M.decide(_theta_with_logits(z), x, L)
+        allowed = [c for c in (L - 1, L, L + 1) if 0 <= c <= 24]
+        assert got in allowed
+        assert z[got] == max(z[c] for c in allowed)

@@ -326,3 +326,17 @@ def test_selection_rule_thresholds(orc):
     assert nl(0, 0.41, 5) == 6 and nl(0, 0.4, 5) == 5 and nl(0, 0.3, 5) == 4
     assert nl(0, 0.2, 5) == 5 and nl(0, 0.1, 5) == 5 and nl(0, 0.3, 0) == 0
     assert nl(0, 0.9, 24) == 24 and nl(1, 0.0, 3) == 4 and nl(2, 0.9, 3) == 3
+
+
+def test_openmp_build_gives_identical_sweeps(orc):
+    """The all-cores build that times the CPU baseline runs the same
+    arithmetic: every sweep result is bit-identical to the plain build's
+    (2D and 3D, several cycles, a ragged grid)."""
+    for n in ([97, 61], [23, 17, 29]):
+        P = orc.Problem(n)
+        f = inputs.uniform_rhs(n, seed=3).ravel()
+        u0 = np.random.default_rng(2).standard_normal(f.size)
+        w = np.concatenate([orc.level_omegas(l) for l in (0, 3, 6, 9)])
+        a = orc.sweeps(P, u0, f, w)
+        b = orc.sweeps(P, u0, f, w, parallel=True)
+        assert np.array_equal(a, b)

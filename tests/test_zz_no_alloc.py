@@ -1,5 +1,6 @@
 """The allocation-free residual-norm entry point (srj_residual_norm_noalloc)
-against the library's ordinary srj_residual_norm, through the C ABI.
+against the FP64 oracle's residual norm and the library's ordinary
+srj_residual_norm, through the C ABI.
 
 It exists for callers that cannot allocate device memory (code running under
 a memory pool or budget it does not own, or on a path where cudaFree's
@@ -32,8 +33,8 @@ def S():
     return srj
 
 
-def _noalloc(S, n, eps, f, u):
-    g = S._grid(n)
+def _noalloc(S, n, eps, f, u, h=None):
+    g = S._grid(n, h=h)
     st = S.srj_stencil()
     for a in range(3):
         st.eps[a] = eps[a] if a < len(eps) else 0.0
@@ -46,16 +47,20 @@ def _noalloc(S, n, eps, f, u):
 
 @pytest.mark.parametrize("n,eps", [([1000], [1.0]), ([300, 200], [0.05, 1.0]),
                                    ([40, 30, 20], [1.0, 0.5, 2.0]), ([4096, 4096], [1.0, 1.0])])
-def test_noalloc_matches_ordinary_entry_point_twice(S, n, eps):
-    f = torch.as_tensor(inputs.uniform_rhs(n, seed=1).ravel(), device="cuda")
+def test_noalloc_matches_ordinary_entry_point_twice(S, orc, n, eps):
+    f_np = inputs.uniform_rhs(n, seed=1).ravel()
+    f = torch.as_tensor(f_np, device="cuda")
+    P = orc.Problem(n, eps=eps)
     h = S.srj_create(n, eps=eps, precision=S.SRJ_PREC_F64)
     try:
         for call in range(2):
-            u = torch.as_tensor(np.random.default_rng(call).standard_normal(f.numel()),
-                                device="cuda")
+            u_np = np.random.default_rng(call).standard_normal(f.numel())
+            u = torch.as_tensor(u_np, device="cuda")
+            want = orc.residual_norm(P, u_np, f_np)
             ref = S.srj_residual_norm(h, f.data_ptr(), u.data_ptr())
             rc, got = _noalloc(S, n, eps, f, u)
             assert rc == S.SRJ_OK
+            assert abs(got - want) <= 1e-12 * want, (call, got, want)
             assert abs(got - ref) <= 1e-12 * ref, (call, got, ref)
     finally:
         S.srj_destroy(h)
@@ -66,3 +71,17 @@ def test_noalloc_rejects_grids_beyond_its_scratch(S):
     f = torch.zeros(2 * 65537, dtype=torch.float64, device="cuda")
     rc, _ = _noalloc(S, n, [1.0, 1.0], f, f)
     assert rc == S.SRJ_EINVAL
+
+
+@pytest.mark.parametrize("bad", ["h_negative", "h_nan", "eps_negative", "eps_inf"])
+def test_noalloc_rejects_bad_spacing_or_coefficient(S, bad):
+    """The same argument checks as srj_create: a negative or non-finite
+    spacing or coefficient is SRJ_EINVAL, never silently replaced."""
+    n = [64, 32]
+    f = torch.zeros(64 * 32, dtype=torch.float64, device="cuda")
+    h = {"h_negative": [-1.0 / 65, 1.0 / 33], "h_nan": [float("nan"), 1.0 / 33]}.get(bad)
+    eps = {"eps_negative": [-1.0, 1.0], "eps_inf": [1.0, float("inf")]}.get(bad, [1.0, 1.0])
+    rc, _ = _noalloc(S, n, eps, f, f, h=h)
+    assert rc == S.SRJ_EINVAL
+    with pytest.raises(S.SrjError):
+        S.srj_create(n, h=h, eps=eps)
