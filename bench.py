@@ -645,12 +645,12 @@ def run_ours(args, rank, world):
         t32 = e0.elapsed_time(e1) * 1e-3
         d32 = args.f32_depth if args.f32_depth else 4
         passes32 = sum(srj.srj_level_m(l) // d32 + 1 for l in levels)
-        pass_s = t32 / passes32
+        pass32_s = t32 / passes32
         hbm_peak32, _ = peaks()
         f32 = {"glups": sw32 * npts / t32 / 1e9, "sweeps": sw32, "seconds": t32,
                "temporal_depth": d32,
-               "hbm_per_pass_gbs": 12.0 * npts / pass_s / 1e9,
-               "hbm_per_pass_frac": 12.0 * npts / pass_s / 1e9 / hbm_peak32,
+               "hbm_per_pass_gbs": 12.0 * npts / pass32_s / 1e9,
+               "hbm_per_pass_frac": 12.0 * npts / pass32_s / 1e9 / hbm_peak32,
                "effective_hbm_frac": 12.0 * sw32 * npts / t32 / 1e9 / hbm_peak32,
                "rel_residual_after": float(rn32[-1] / rn32[0]) if len(rn32) else None,
                "schedule": "levels 0..16 then 16 x20"}
