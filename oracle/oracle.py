@@ -117,6 +117,13 @@ def _declare(L):
     L.oracle_mg_solve.argtypes = [pp, dp, dp, C.c_double, C.c_int, C.c_int, C.c_int,
                                   C.c_long, lp, dp, dp, dp]
     L.oracle_mg_solve.restype = C.c_int
+    L.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+    L.oracle_splitmix64.restype = C.c_uint64
+    L.oracle_pick.argtypes = [C.c_uint64, C.c_long, C.c_long, C.c_int]
+    L.oracle_pick.restype = C.c_int
+    L.oracle_collect_moves.argtypes = [pp, dp, C.c_double, C.c_int, C.c_uint64, C.c_long,
+                                       C.c_long, dp, ip, ip, dp, dp, lp, ip]
+    L.oracle_collect_moves.restype = C.c_long
     return L
 
 
@@ -343,3 +350,33 @@ def mg_solve(P: Problem, f, u0=None, tol=1e-8, level=0, nu1=1, nu2=1, max_cycles
                                int(max_cycles), C.byref(cy), C.byref(r0), C.byref(rn), _dp(tr))
     return dict(u=u, status=st, cycles=cy.value, r0=r0.value, rn=rn.value,
                 rns=tr[:cy.value].copy())
+
+
+def splitmix64(seed: int, index: int) -> int:
+    return lib().oracle_splitmix64(seed, index)
+
+
+def pick(seed: int, trial: int, step: int, ncand: int) -> int:
+    return lib().oracle_pick(seed, trial, step, ncand)
+
+
+def collect_moves(P: Problem, f, tol=1e-8, max_level=24, seed=0, trial=0, max_steps=100000):
+    """One trial of the Sec. 3 data collection (see oracle_collect_moves).
+    Returns the records (prev_ratio, level, action, r_before, r_after) and
+    the levels taken (level 0 of the first cycle, then one per step)."""
+    f = _f64(f).ravel()
+    cap = 3 * max_steps
+    pr = np.zeros(cap)
+    lv = np.zeros(cap, dtype=np.int32)
+    ac = np.zeros(cap, dtype=np.int32)
+    rb = np.zeros(cap)
+    ra = np.zeros(cap)
+    taken = np.zeros(max_steps + 1, dtype=np.int32)
+    nrec = C.c_long()
+    ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+    steps = lib().oracle_collect_moves(P._c(), _dp(f), float(tol), int(max_level), int(seed),
+                                       int(trial), int(max_steps), _dp(pr), ip(lv), ip(ac),
+                                       _dp(rb), _dp(ra), C.byref(nrec), ip(taken))
+    n = nrec.value
+    return dict(prev_ratio=pr[:n], level=lv[:n], action=ac[:n], r_before=rb[:n],
+                r_after=ra[:n], steps=steps, taken=taken[:steps + 1])

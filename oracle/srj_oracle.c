@@ -24,6 +24,7 @@
  *  - the first cycle runs at level 0; a decision follows every cycle.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -630,4 +631,97 @@ int oracle_mg_solve(const oracle_problem *P, const double *f, double *u, double 
     if (r0_out) *r0_out = r0;
     if (rn_out) *rn_out = rn;
     return status;
+}
+
+/* ------------------------------------------------------------------------
+ * Sec. 3 data collection (the procedure the heuristic of Alg. 1 was read
+ * from).  A trial starts from x = 0 and applies one cycle at level 0; the
+ * residual ratio after / before it and the level form the state.  Each later
+ * step tries every allowed move from the current iterate -- decrease, keep,
+ * increase the level, inside [0, max_level] -- one cycle each, and records
+ * for each the state (previous ratio, current level), the move and the
+ * residual norms before and after its cycle (its average convergence rate is
+ * -log(after / before) / M, Eq. average-convergence-rate).  One of the tried
+ * moves is then taken at random: its iterate, level and ratio become the next
+ * state.  The trial ends once the taken iterate's residual norm is below tol
+ * (the paper uses 1e-8), or after max_steps steps.
+ *
+ * The random move comes from a counter-based generator: the output function
+ * of SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014) applied to the counter value
+ * seed + (index + 1) * 0x9E3779B97F4A7C15, index = trial * 2^32 + step; the
+ * move is candidate floor(u * ncand), u = (output >> 11) * 2^-53, computed
+ * in integers.
+ * ------------------------------------------------------------------------ */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t index)
+{
+    uint64_t z = seed + (index + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int oracle_pick(uint64_t seed, long trial, long step, int ncand)
+{
+    const uint64_t index = ((uint64_t)trial << 32) + (uint64_t)step;
+    const uint64_t bits = oracle_splitmix64(seed, index) >> 11;
+    return (int)((bits * (uint64_t)ncand) >> 53);
+}
+
+/* One trial.  Records go to the arrays at positions 0 .. *nrec_out - 1
+ * (capacity 3 * max_steps); the levels taken after the first cycle go to
+ * taken_levels (capacity max_steps + 1, may be NULL).  Returns the number of
+ * steps made. */
+long oracle_collect_moves(const oracle_problem *P, const double *f, double tol, int max_level,
+                          uint64_t seed, long trial, long max_steps, double *prev_ratio,
+                          int *level, int *action, double *r_before, double *r_after,
+                          long *nrec_out, int *taken_levels)
+{
+    const long N = or_npts(P);
+    double *u = (double *)calloc((size_t)N, sizeof(double));
+    double *w[3];
+    for (int c = 0; c < 3; ++c) w[c] = (double *)malloc(sizeof(double) * (size_t)N);
+    double *omega = (double *)malloc(sizeof(double) * 2362);
+    const double r0 = oracle_residual_norm(P, u, f);
+    /* the first cycle, at level 0 */
+    int M = oracle_level_omegas(0, omega);
+    oracle_sweeps(P, u, f, omega, M);
+    double rcur = oracle_residual_norm(P, u, f);
+    double prev = r0 > 0.0 ? rcur / r0 : 0.0;
+    int L = 0;
+    if (taken_levels) taken_levels[0] = 0;
+    long nrec = 0, step = 0;
+    for (; step < max_steps && !(rcur < tol); ++step) {
+        int cand_level[3], cand_action[3], ncand = 0;
+        double rc[3];
+        for (int a = -1; a <= 1; ++a) {
+            const int c = L + a;
+            if (c < 0 || c > max_level) continue;
+            memcpy(w[ncand], u, sizeof(double) * (size_t)N);
+            M = oracle_level_omegas(c, omega);
+            oracle_sweeps(P, w[ncand], f, omega, M);
+            rc[ncand] = oracle_residual_norm(P, w[ncand], f);
+            cand_level[ncand] = c;
+            cand_action[ncand] = a;
+            prev_ratio[nrec] = prev;
+            level[nrec] = L;
+            action[nrec] = a;
+            r_before[nrec] = rcur;
+            r_after[nrec] = rc[ncand];
+            ++nrec;
+            ++ncand;
+        }
+        const int k = oracle_pick(seed, trial, step, ncand);
+        memcpy(u, w[k], sizeof(double) * (size_t)N);
+        prev = rc[k] / rcur;
+        rcur = rc[k];
+        L = cand_level[k];
+        (void)cand_action;
+        if (taken_levels) taken_levels[step + 1] = L;
+    }
+    *nrec_out = nrec;
+    free(u);
+    for (int c = 0; c < 3; ++c) free(w[c]);
+    free(omega);
+    return step;
 }
