@@ -470,7 +470,7 @@ def selector_leg(srj, inputs, torch, stream, seed=0):
     return out
 
 
-def vark3d_leg(srj, inputs, torch, stream, seed=0, side=512, fp64=True):
+def vark3d_leg(srj, inputs, torch, stream, seed=0, side=512, fp64=True, depth=0):
     """3D variable-coefficient diffusion -div(k grad u) = f, 7-point stencil,
     harmonic-mean faces, log k Gaussian random field (correlation 16 cells,
     sigma 1), f ~ N(0,1), rel 1e-8: mixed precision (FP32-pair inner SRJ
@@ -484,7 +484,8 @@ def vark3d_leg(srj, inputs, torch, stream, seed=0, side=512, fp64=True):
     for label, prec in (("mixed", srj.SRJ_PREC_MIXED), ("plain_fp64", srj.SRJ_PREC_F64)):
         if label == "plain_fp64" and not fp64:
             continue
-        h = srj.srj_create(n, k_ptr=kt.data_ptr(), precision=prec, stream=stream.cuda_stream)
+        h = srj.srj_create(n, k_ptr=kt.data_ptr(), precision=prec, stream=stream.cuda_stream,
+                           temporal_depth=depth if label == "mixed" else 0)
         u = torch.zeros_like(f)
         st = srj.srj_solve(h, f.data_ptr(), u.data_ptr(), TOL)
         srj.srj_destroy(h)
@@ -672,7 +673,7 @@ def run_ours(args, rank, world):
     vark = None
     if not args.no_3d:
         vark = vark3d_leg(srj, inputs, torch, stream, seed=rank, side=args.side3d,
-                          fp64=not args.no_fp64)
+                          fp64=not args.no_fp64, depth=args.depth3d)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -749,6 +750,8 @@ def main():
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D variable-k leg")
     ap.add_argument("--with-3d", action="store_true", help=argparse.SUPPRESS)  # the default now
     ap.add_argument("--side3d", type=int, default=512)
+    ap.add_argument("--depth3d", type=int, default=0,
+                    help="sweeps per pass of the 3D mixed solve (0: library choice)")
     ap.add_argument("--f32-depth", type=int, default=0, help="temporal depth of the FP32 leg")
     ap.add_argument("--depth", type=int, default=0, help="temporal depth of the inner pass (0: library)")
     ap.add_argument("--side", type=int, default=SIDE, help="grid side (profiling runs only)")

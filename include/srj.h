@@ -63,7 +63,11 @@ enum srj_selector {
     SRJ_SEL_HEURISTIC = 0,  /* Sec. 3, Alg. 1: ratio > 0.4 up, 0.2 < ratio < 0.4 down */
     SRJ_SEL_INCREASING = 1, /* Sec. 4: raise the level every cycle */
     SRJ_SEL_FIXED = 2,      /* stay at opts.fixed_level */
-    SRJ_SEL_MLP = 3         /* learned selector (srj_mlp_set_weights), Alg. 1 as fallback */
+    SRJ_SEL_MLP = 3,        /* learned selector (srj_mlp_set_weights), Alg. 1 as fallback */
+    SRJ_SEL_JACOBI = 4      /* plain Jacobi, Sec. 2 Eq. (jacobi): omega = 1 every sweep, the
+                               comparator of Sec. 4 and Table 3; the residual is tested
+                               after every M(fixed_level) sweeps (a "cycle"; level 0:
+                               every sweep).  Single-grid handles only. */
 };
 
 /* Arithmetic of the sweeps; f and u element types follow it. */
@@ -133,7 +137,10 @@ typedef struct srj_opts {
     int32_t level0;         /* level of the first cycle (Sec. 3 uses 0) */
     int32_t fixed_level;    /* level for SRJ_SEL_FIXED */
     int32_t max_level;      /* highest selectable level, <= 24 (0 means 24) */
-    int32_t temporal_depth; /* sweeps fused per HBM pass; 0 = library choice */
+    int32_t temporal_depth; /* sweeps fused per HBM pass; 0 = library choice.
+                               2D constant coefficients: 1 or 2 (F64), 4 or 8
+                               (F32), 2 or 4 (MIXED); 3D Dirichlet: 1 or 2
+                               (default 2 for MIXED, 1 otherwise) */
     int32_t trace_capacity; /* per-cycle records kept (0 means 4096) */
     int64_t max_sweeps;     /* sweep cap per solve (0 means 1000000) */
     double inner_tol;       /* SRJ_PREC_MIXED: floor of the inner solves' relative
@@ -328,6 +335,42 @@ srj_status srj_mg_create(const srj_grid *grid, const srj_stencil *stencil,
  * The handle must come from srj_mg_create (SRJ_EINVAL otherwise). */
 srj_status srj_mg_solve(srj_handle *h, const double *f, double *u, double tol,
                         srj_stats *stats);
+
+/* One record of the Sec. 3 data collection (srj_collect_moves). */
+typedef struct srj_move_record {
+    double prev_ratio; /* state: ||r|| after / before the previous cycle taken */
+    double r_before;   /* ||b - A x|| before the tried cycle */
+    double r_after;    /* ||b - A x|| after it; the move's average convergence
+                          rate (Sec. 3, Eq. average-convergence-rate) is
+                          -log(r_after / r_before) / M(level + action) */
+    int32_t level;     /* state: the current scheme level */
+    int32_t action;    /* the tried move: -1 decrease, 0 keep, +1 increase */
+} srj_move_record;
+
+/* Sec. 3, data collection: trials of the procedure the paper derived Alg. 1
+ * from, on the 1D Poisson system of Sec. 3 (Eq. poisson: N = n interior
+ * points, h = 1/(n+1), zero Dirichlet values), FP64.  A trial starts from
+ * x = 0 with one cycle at level 0; at every step it tries each allowed move
+ * (decrease, keep, increase the level, inside [0, max_level]) from the
+ * current iterate, one cycle each, records them, and takes one at random (the
+ * taken cycle's iterate, level and ratio are the next state); it ends once
+ * the taken residual norm is below tol (the paper: 1e-8) or after max_steps
+ * steps.  The move of step k of trial t is candidate floor(u * ncand) of the
+ * allowed moves in the order decrease, keep, increase, where u = (z >> 11) *
+ * 2^-53 and z is SplitMix64's output function (Steele, Lea and Flood, 2014)
+ * applied to seed + (t * 2^32 + k + 1) * 0x9E3779B97F4A7C15.
+ *
+ * f: DEVICE array of n values, or NULL for b = 1 (the paper's choice).  Runs
+ * trials trial0 .. trial0 + ntrials - 1; trial trial0 + i writes its records
+ * to out[i * 3 * max_steps ...] (DEVICE, ntrials * 3 * max_steps records,
+ * caller-owned) and their number to counts[i] (DEVICE, ntrials).  n is
+ * limited to 4096 (each trial lives in one CTA's shared memory): SRJ_EINVAL
+ * beyond, for ntrials < 1, max_steps < 1, a max_level outside [0, 24] or tol
+ * not a positive finite number.  Allocates and frees a small factor table,
+ * runs on `stream` and synchronises it. */
+srj_status srj_collect_moves(int64_t n, const double *f, double tol, int32_t max_level,
+                             uint64_t seed, int64_t trial0, int32_t ntrials, int32_t max_steps,
+                             srj_move_record *out, int32_t *counts, void *stream);
 
 /* Failure detection (the paper has no counterpart): the 3D pass waits for
  * every plane it stages in shared memory at most `polls` polls of its

@@ -102,22 +102,25 @@ __global__ void __launch_bounds__(kTX * kTY)
     __shared__ int s_err;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kTX * ty;
+    __shared__ int s_skip;
     if (tid == 0) {
         s_plan = plan_pass(a, 1);
+        // beside the two-sweep kernel this one runs only a cycle's tail
+        s_skip = s_plan.run && a.tail_only && !pass_is_tail(a.st, a.lvl_m);
         s_omega = (s_plan.run && s_plan.nsw) ? a.w64[s_plan.woff] : 0.0;
         s_wlim = a.st->wait_limit;
         s_err = 0;
         if (!s_plan.run && a.cfg.use_cond && blockIdx.x == 0 && blockIdx.y == 0 &&
             blockIdx.z == 0)
             cudaGraphSetConditional(a.cfg.cond, 0);
-        if (s_plan.run) {
+        if (s_plan.run && !s_skip) {
             for (int k = 0; k < kNS; ++k) bar_init(&s_bar[k]);
             asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         }
     }
     __syncthreads();
     const PassPlan p = s_plan;
-    if (!p.run) return;
+    if (!p.run || s_skip) return;
     const double omega = s_omega;
     const long long wlim = s_wlim;
 
@@ -262,6 +265,302 @@ __global__ void __launch_bounds__(kTX * kTY)
     finish_pass(a, p, tot, dinf);
 }
 
+// ---------------------------------------------------------------------------
+// Two sweeps per pass (temporal blocking along z, 2.5D).  A CTA of 32 x 8
+// threads owns a 32 x 16 output tile and walks a chunk of z planes.  Input
+// planes (iterate, rhs and, for variable coefficients, the face weights and
+// 1/D) arrive by TMA in one box shape {40, 20} from (x0 - 4, y0 - 2): four
+// ring slots, planes issued up to three ahead.  At step z, level 1 (the first
+// sweep of the pass) computes plane z on the tile plus a one-cell halo (34 x
+// 18 points, a fixed set of two or three per thread) into a two-plane ring of
+// level-1 values; after a block barrier, level 2 (the second sweep) computes
+// plane z - 1 of the tile (two points per thread) from the level-1 ring and
+// stores it.  Each thread carries the z neighbours of its points and the
+// -z face weights in registers from plane to plane, and level 2 reads the
+// coefficients of its next plane one step ahead, so no slot is needed after
+// the step that last reads it.  Level-1 values outside the grid are zero (the
+// Dirichlet ghosts).  Only passes of two sweeps run here; the last pass of a
+// cycle (fewer sweeps, the residual) runs in plane3d_kernel.
+constexpr int kT2Y = 16;              // output rows per tile (two per thread)
+constexpr int kBW = 40, kBH = 20;     // staged box: columns x0-4 .., rows y0-2 ..
+constexpr int kL1W = 34, kL1H = 18;   // level-1 region: columns x0-1 .., rows y0-1 ..
+constexpr int kL1N = kL1W * kL1H;     // 612 points
+constexpr int kNS2 = 4;               // input ring slots
+constexpr int kT2Threads = kTX * kTY;  // 256
+
+template <int PREC, bool VARK>
+struct Plane2 {
+    using T = typename Elem<PREC>::T;
+    static constexpr bool LO = PREC == PREC_DF;
+    static constexpr int ES = PREC == PREC_F64 ? 8 : 4;
+    static constexpr int BOX = kBW * kBH * ES;  // bytes of one staged array (multiple of 128)
+    static constexpr int o_hi = 0, o_lo = BOX, o_f = o_lo + (LO ? BOX : 0);
+    static constexpr int o_wx = o_f + BOX, o_wy = o_wx + (VARK ? BOX : 0);
+    static constexpr int o_wz = o_wy + (VARK ? BOX : 0), o_id = o_wz + (VARK ? BOX : 0);
+    static constexpr int BYTES = o_id + (VARK ? BOX : 0);    // one ring slot
+    static constexpr unsigned TX = (unsigned)BYTES;          // bytes a plane's copies deliver
+    static constexpr int L1B = al128(kL1N * (int)sizeof(T));  // one level-1 plane
+    static constexpr int SMEM = kNS2 * BYTES + 2 * L1B;
+    static constexpr int MINB = SMEM > 113 * 1024 ? 1 : 2;   // CTAs per SM the smem allows
+};
+
+template <int PREC, bool VARK>
+__global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
+    plane3d2_kernel(PassLaunch a, int zchunk, const __grid_constant__ Plane3dMaps maps) {
+    using T = typename Elem<PREC>::T;
+    using C = typename Elem<PREC>::C;
+    using P = Point<PREC, 3>;
+    using L = Plane2<PREC, VARK>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_bar[kNS2];
+    __shared__ PassPlan s_plan;
+    __shared__ double s_om[2];
+    __shared__ long long s_wlim;
+    __shared__ int s_mine, s_err;
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kTX * ty;
+    if (tid == 0) {
+        s_plan = plan_pass(a, 2);
+        // this kernel runs the passes of two sweeps; the rest of a cycle (and
+        // the residual) belongs to the one-sweep kernel launched beside it
+        s_mine = s_plan.run && s_plan.nsw == 2 && !s_plan.resid;
+        s_om[0] = s_mine ? a.w64[s_plan.woff] : 0.0;
+        s_om[1] = s_mine ? a.w64[s_plan.woff + 1] : 0.0;
+        s_wlim = a.st->wait_limit;
+        s_err = 0;
+        if (!s_plan.run && a.cfg.use_cond && blockIdx.x == 0 && blockIdx.y == 0 &&
+            blockIdx.z == 0)
+            cudaGraphSetConditional(a.cfg.cond, 0);
+        if (s_mine) {
+            for (int k = 0; k < kNS2; ++k) bar_init(&s_bar[k]);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
+    }
+    __syncthreads();
+    if (!s_mine) return;
+    const PassPlan p = s_plan;
+    const double om1 = s_om[0], om2 = s_om[1];
+    const long long wlim = s_wlim;
+
+    const GridGeo &g = a.geo;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kT2Y;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, g.nz);
+    const int src = p.cur, dst = p.cur ^ 1;
+    unsigned char *l1b = smem + kNS2 * L::BYTES;  // two level-1 planes
+
+    // plane zz (>= z0 - 2) lives in slot (zz - z0 + 2) mod 4; the n-th plane
+    // of a slot completes its barrier's phase n
+    auto rel = [&](int zz) { return zz - (z0 - 2); };
+    auto slot = [&](int zz) -> unsigned char * { return smem + (rel(zz) % kNS2) * L::BYTES; };
+    auto issue = [&](int zz) {  // one thread
+        unsigned char *s = slot(zz);
+        uint64_t *bar = &s_bar[rel(zz) % kNS2];
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        bar_expect(bar, L::TX);
+        const int xs = x0 - kHX, ys = y0 - 2;
+        tma3(s + L::o_hi, &maps.u[src], xs, ys, zz, bar);
+        if constexpr (L::LO) tma3(s + L::o_lo, &maps.ulo[src], xs, ys, zz, bar);
+        tma3(s + L::o_f, &maps.f, xs, ys, zz, bar);
+        if constexpr (VARK) {
+            tma3(s + L::o_wx, &maps.wx, xs, ys, zz, bar);
+            tma3(s + L::o_wy, &maps.wy, xs, ys, zz, bar);
+            tma3(s + L::o_wz, &maps.wz, xs, ys, zz, bar);
+            tma3(s + L::o_id, &maps.invd, xs, ys, zz, bar);
+        }
+    };
+    auto wait = [&](int zz, long long limit) -> bool {
+        return bar_wait(&s_bar[rel(zz) % kNS2], (unsigned)((rel(zz) / kNS2) & 1), limit);
+    };
+    // staged arrays: index of column lx (-4 .. 35), row ly (-2 .. 17) of the tile
+    auto sidx = [](int lx, int ly) { return (lx + kHX) + kBW * (ly + 2); };
+    auto ldc = [&](const unsigned char *s, int off, int i) -> C {
+        return *(const C *)(s + off + i * L::ES);
+    };
+    auto ldu = [&](const unsigned char *s, int i) -> T {
+        if constexpr (L::LO)
+            return df32{*(const float *)(s + L::o_hi + i * 4), *(const float *)(s + L::o_lo + i * 4)};
+        else
+            return *(const T *)(s + L::o_hi + i * L::ES);
+    };
+    auto l1 = [&](int zz) -> T * { return (T *)(l1b + (zz & 1) * L::L1B); };
+
+    C cconst[3];
+    const C invd_c = C(g.invdiag);
+    cconst[0] = C(g.acx);
+    cconst[1] = C(g.acy);
+    cconst[2] = C(g.acz);
+
+    // level-1 points of this thread: q = tid + 256 k, column q % 34 - 1,
+    // row q / 34 - 1 of the tile; and level-2 points: column tx, rows ty, ty + 8
+    constexpr int K1 = (kL1N + kT2Threads - 1) / kT2Threads;  // 3
+    int si1[K1];
+    bool has1[K1], in1[K1];
+#pragma unroll
+    for (int k = 0; k < K1; ++k) {
+        const int q = tid + kT2Threads * k;
+        has1[k] = q < kL1N;
+        const int lx = q % kL1W - 1, ly = q / kL1W - 1;
+        si1[k] = sidx(lx, ly);
+        const int gx = x0 + lx, gy = y0 + ly;
+        in1[k] = has1[k] && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
+    }
+    int si2[2], li2[2];
+    bool in2[2];
+    long long col2[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int ly = ty + 8 * q;
+        si2[q] = sidx(tx, ly);
+        li2[q] = (tx + 1) + kL1W * (ly + 1);
+        in2[q] = (x0 + tx) < g.nx && (y0 + ly) < g.ny;
+        col2[q] = (long long)(x0 + tx) + g.pitch * (y0 + ly);
+    }
+
+    if (tid == 0)
+        for (int zz = z0 - 2; zz <= min(z0 + 1, z1 + 1); ++zz) issue(zz);
+    int last_issued = min(z0 + 1, z1 + 1);
+    int next_wait = z0 - 2;  // first plane this thread has not seen land
+    bool ok = true;
+
+    // carried values: level 1 -- the iterate at z - 1 and z and the -z face;
+    // level 2 -- level-1 values at z - 2 and z - 1 and the coefficients of the
+    // plane it computes next
+    T um1[K1], uc1[K1];
+    C wzm1[K1];
+#pragma unroll
+    for (int k = 0; k < K1; ++k) {
+        um1[k] = zero_u<PREC>();
+        uc1[k] = zero_u<PREC>();
+        wzm1[k] = C(0);
+    }
+    T vm2[2], vc2[2];
+    C cf[2], cwxm[2], cwxp[2], cwym[2], cwyp[2], cwzm[2], cwzp[2], cid[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        vm2[q] = zero_u<PREC>();
+        vc2[q] = zero_u<PREC>();
+        cf[q] = cwxm[q] = cwxp[q] = cwym[q] = cwyp[q] = cwzm[q] = cwzp[q] = C(0);
+        cid[q] = invd_c;
+    }
+
+    for (int z = z0 - 1; z <= z1; ++z) {
+        // planes z and z + 1 (and, at the first step, z - 1) must have landed
+        while (ok && next_wait <= z + 1) {
+            if (wait(next_wait, wlim)) ++next_wait;
+            else ok = false;
+        }
+        // one decision for the block; the barrier also means every thread is
+        // done with the previous step, so the slot of plane z - 1 is free
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        {
+            // plane z + 3 goes into the slot plane z - 1 held (at the first
+            // step that slot's plane z0 - 2 is still read: one plane less)
+            const int lim = min(z == z0 - 1 ? z + 2 : z + 3, z1 + 1);
+            if (tid == 0)
+                for (int pl = last_issued + 1; pl <= lim; ++pl) issue(pl);
+            if (lim > last_issued) last_issued = lim;
+        }
+        const unsigned char *s0 = slot(z), *sp = slot(z + 1);
+        const bool zin = z >= 0 && z < g.nz;
+        T *l1z = l1(z);
+        // level 1: plane z of the tile plus halo
+#pragma unroll
+        for (int k = 0; k < K1; ++k) {
+            if (!has1[k]) continue;
+            const int i = si1[k];
+            if (z == z0 - 1) {  // the first step reads what later steps carry
+                const unsigned char *sm = slot(z - 1);
+                um1[k] = ldu(sm, i);
+                uc1[k] = ldu(s0, i);
+                if constexpr (VARK) wzm1[k] = ldc(sm, L::o_wz, i);
+            }
+            const T up = ldu(sp, i);
+            T val = zero_u<PREC>();
+            C wzp = C(0);
+            if constexpr (VARK) wzp = ldc(s0, L::o_wz, i);
+            if (in1[k] && zin) {
+                T nb[6];
+                nb[0] = ldu(s0, i - 1);
+                nb[1] = ldu(s0, i + 1);
+                nb[2] = ldu(s0, i - kBW);
+                nb[3] = ldu(s0, i + kBW);
+                nb[4] = um1[k];
+                nb[5] = up;
+                const C fi = ldc(s0, L::o_f, i);
+                T t;
+                if constexpr (VARK) {
+                    C wgt[6];
+                    wgt[0] = ldc(s0, L::o_wx, i - 1);
+                    wgt[1] = ldc(s0, L::o_wx, i);
+                    wgt[2] = ldc(s0, L::o_wy, i - kBW);
+                    wgt[3] = ldc(s0, L::o_wy, i);
+                    wgt[4] = wzm1[k];
+                    wgt[5] = wzp;
+                    t = P::t_of(nb, wgt, ldc(s0, L::o_id, i), fi, uc1[k]);
+                } else {
+                    t = P::t_const(nb, cconst, invd_c, fi, uc1[k]);
+                }
+                val = P::relax(uc1[k], t, om1);
+            }
+            l1z[tid + kT2Threads * k] = val;
+            um1[k] = uc1[k];
+            uc1[k] = up;
+            if constexpr (VARK) wzm1[k] = wzp;
+        }
+        __syncthreads();
+        // level 2: plane z - 1 of the tile, from level-1 planes z - 2 (carried),
+        // z - 1 (ring: neighbours, carried: centre) and z (ring)
+        const T *l1m = l1(z - 1);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const T vp = l1z[li2[q]];
+            if (z - 1 >= z0 && in2[q]) {
+                T nb[6];
+                nb[0] = l1m[li2[q] - 1];
+                nb[1] = l1m[li2[q] + 1];
+                nb[2] = l1m[li2[q] - kL1W];
+                nb[3] = l1m[li2[q] + kL1W];
+                nb[4] = vm2[q];
+                nb[5] = vp;
+                T t;
+                if constexpr (VARK) {
+                    C wgt[6] = {cwxm[q], cwxp[q], cwym[q], cwyp[q], cwzm[q], cwzp[q]};
+                    t = P::t_of(nb, wgt, cid[q], cf[q], vc2[q]);
+                } else {
+                    t = P::t_const(nb, cconst, invd_c, cf[q], vc2[q]);
+                }
+                store_u<PREC>(a.bufs, dst, col2[q] + (long long)g.plane * (z - 1),
+                              P::relax(vc2[q], t, om2));
+            }
+            vm2[q] = vc2[q];
+            vc2[q] = vp;
+            // the coefficients of plane z, for the next step
+            const int i = si2[q];
+            cf[q] = ldc(s0, L::o_f, i);
+            if constexpr (VARK) {
+                cwxm[q] = ldc(s0, L::o_wx, i - 1);
+                cwxp[q] = ldc(s0, L::o_wx, i);
+                cwym[q] = ldc(s0, L::o_wy, i - kBW);
+                cwyp[q] = ldc(s0, L::o_wy, i);
+                cwzm[q] = cwzp[q];
+                cwzp[q] = ldc(s0, L::o_wz, i);
+                cid[q] = ldc(s0, L::o_id, i);
+            }
+        }
+    }
+    // every copy in flight lands before the shared memory goes away (the
+    // drain uses the default limit); a wait that ran out marks the solve
+    for (; next_wait <= last_issued; ++next_wait) ok = wait(next_wait, kDefaultWaitLimit) && ok;
+    if (!ok) atomicOr(&s_err, 1);
+    __syncthreads();
+    if (s_err && tid == 0) atomicExch(&a.st->status, (int)DST_TIMEOUT);
+    finish_pass(a, p, 0.0);
+}
+
 template <int PREC, bool VARK>
 void *plane_entry() {
     return (void *)&plane3d_kernel<PREC, VARK>;
@@ -286,6 +585,49 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 }  // namespace
 
 int plane3d_zchunk(const GridGeo &g) { return g.nz < 32 ? g.nz : 32; }
+
+template <int PREC, bool VARK>
+void *plane2_entry() {
+    return (void *)&plane3d2_kernel<PREC, VARK>;
+}
+
+Plane3dPlan plane3d2_plan(int prec, const GridGeo &g, bool vark, int num_sms) {
+    Plane3dPlan p{};
+    p.block = dim3(kTX, kTY, 1);
+    int minb = 2;
+#define P2_(PR, VK)                                  \
+    do {                                             \
+        p.kernel = plane2_entry<PR, VK>();           \
+        p.smem = Plane2<PR, VK>::SMEM;               \
+        minb = Plane2<PR, VK>::MINB;                 \
+    } while (0)
+    if (prec == PREC_F64) {
+        if (vark) P2_(PREC_F64, true); else P2_(PREC_F64, false);
+    } else if (prec == PREC_F32) {
+        if (vark) P2_(PREC_F32, true); else P2_(PREC_F32, false);
+    } else {
+        if (vark) P2_(PREC_DF, true); else P2_(PREC_DF, false);
+    }
+#undef P2_
+    // z chunks: at least four waves of CTAs over the SMs, 16 .. 64 planes each
+    // (each chunk computes two extra level-1 planes and stages three extra)
+    long long cxy = (long long)((g.nx + kTX - 1) / kTX) * ((g.ny + kT2Y - 1) / kT2Y);
+    if (cxy < 1) cxy = 1;
+    const long long want = (4LL * num_sms * minb + cxy - 1) / cxy;
+    long long zc = (g.nz + want - 1) / (want > 0 ? want : 1);
+    if (zc < 16) zc = 16;
+    if (zc > 64) zc = 64;
+    if (zc > g.nz) zc = g.nz;
+    p.zchunk = (int)zc;
+    p.grid = dim3((g.nx + kTX - 1) / kTX, (g.ny + kT2Y - 1) / kT2Y,
+                  (unsigned)((g.nz + zc - 1) / zc));
+    return p;
+}
+
+cudaError_t plane3d2_prepare(int prec, bool vark) {
+    const Plane3dPlan q = plane3d2_plan(prec, GridGeo{}, vark, 1);
+    return cudaFuncSetAttribute(q.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, q.smem);
+}
 
 Plane3dPlan plane3d_plan(int prec, const GridGeo &g, bool vark) {
     Plane3dPlan p{};
@@ -315,7 +657,7 @@ cudaError_t plane3d_prepare(int prec, bool vark) {
 // (row stride pitch, plane stride pitch * ny elements), boxes as in Plane.
 // Coordinates outside {nx, ny, nz} read as zero.
 cudaError_t plane3d_encode(int prec, bool vark, const GridGeo &g, const IterBufs &b,
-                           Plane3dMaps *m) {
+                           Plane3dMaps *m, bool two_sweep) {
     static EncodeTiledFn encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -345,6 +687,20 @@ cudaError_t plane3d_encode(int prec, bool vark, const GridGeo &g, const IterBufs
     auto ck = [&](cudaError_t x) {
         if (x != cudaSuccess && e == cudaSuccess) e = x;
     };
+    if (two_sweep) {  // every array in the one box of the two-sweep pass
+        for (int k = 0; k < 2; ++k) {
+            ck(enc(&m->u[k], b.u[k], kBW, kBH));
+            if (prec == PREC_DF) ck(enc(&m->ulo[k], b.ulo[k], kBW, kBH));
+        }
+        ck(enc(&m->f, b.f, kBW, kBH));
+        if (vark) {
+            ck(enc(&m->wx, b.wx, kBW, kBH));
+            ck(enc(&m->wy, b.wy, kBW, kBH));
+            ck(enc(&m->wz, b.wz, kBW, kBH));
+            ck(enc(&m->invd, b.invd, kBW, kBH));
+        }
+        return e;
+    }
     for (int k = 0; k < 2; ++k) {
         ck(enc(&m->u[k], b.u[k], kSX, kTY + 2));
         if (prec == PREC_DF) ck(enc(&m->ulo[k], b.ulo[k], kSX, kTY + 2));

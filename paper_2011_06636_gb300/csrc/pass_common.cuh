@@ -37,14 +37,25 @@ __device__ __forceinline__ PassPlan plan_pass(const DevState *st, const int *lvl
         p.resid = 1;
         return p;
     }
-    const int M = lvl_m[st->level];
+    // plain Jacobi (Sec. 2, Eq. jacobi): cycles of M(fixed_level) sweeps
+    // with omega = 1, read from the ones at the end of the factor tables
+    const bool jac = st->selector == DSEL_JACOBI;
+    const int M = lvl_m[jac ? st->fixed_level : st->level];
     const int rem = M - st->k;
     // A cycle of M sweeps takes floor(M / depth) + 1 passes; the last one does
     // rem < depth sweeps and then the residual of the cycle's final state.
     p.nsw = rem >= depth ? depth : rem;
     p.resid = rem < depth ? 1 : 0;
-    p.woff = lvl_off[st->level] + st->k;
+    p.woff = jac ? kTotalOmegas : lvl_off[st->level] + st->k;
     return p;
+}
+
+// With a two-sweep kernel beside it, a one-sweep kernel runs only the tail of
+// a cycle: the initial residual, a single remaining sweep, the residual.
+__device__ __forceinline__ bool pass_is_tail(const DevState *st, const int *lvl_m) {
+    if (st->phase == 0) return true;
+    const bool jac = st->selector == DSEL_JACOBI;
+    return lvl_m[jac ? st->fixed_level : st->level] - st->k < 2;
 }
 
 __device__ __forceinline__ PassPlan plan_pass(const PassLaunch &a, int depth) {
@@ -69,6 +80,8 @@ __device__ __forceinline__ int next_level(DevState *st, const SolveCfg &cfg, dou
             return level < top ? level + 1 : level;
         case DSEL_FIXED:
             return st->fixed_level;
+        case DSEL_JACOBI:  // no scheme level: every cycle is M(fixed_level) plain sweeps
+            return level;
         case DSEL_SCHEDULE:
             return (st->cycles < st->nsched) ? cfg.sched[st->cycles] : level;
         default:  // Alg. 1 (also the fallback of the learned selector)

@@ -28,6 +28,10 @@ constexpr int kNumLevels = 25;
 // are then still drained with this limit.
 constexpr long long kDefaultWaitLimit = 1LL << 22;
 constexpr int kTotalOmegas = 9710;  // sum of M over the 25 levels
+// The factor tables end with kJacobiOnes factors omega = 1 (at offset
+// kTotalOmegas): every pass of a plain-Jacobi solve reads its factors there.
+constexpr int kJacobiOnes = 8;
+constexpr int kTableOmegas = kTotalOmegas + kJacobiOnes;
 
 // App. B table (scheme level -> M) and the offset of each level's factors in
 // the concatenated factor table.  Defined in schemes.cpp.
@@ -43,7 +47,8 @@ enum DevSelector : int32_t {
     DSEL_INCREASING = 1,
     DSEL_FIXED = 2,
     DSEL_MLP = 3,
-    DSEL_SCHEDULE = 4  // explicit level list (srj_run_levels)
+    DSEL_JACOBI = 4,   // plain Jacobi (omega = 1), residual every M(fixed_level) sweeps
+    DSEL_SCHEDULE = 5  // explicit level list (srj_run_levels)
 };
 
 // Status values of a device-side solve.
@@ -158,6 +163,7 @@ struct PassLaunch {
     int lvl_m[kNumLevels];    // App. B: M of each level
     int lvl_off[kNumLevels];  // offset of each level's factors in w64 / w32
     int dinf;                 // 1: sweep passes also reduce max |u' - u| (SRJ_TOL_DINF)
+    int tail_only;            // 1: the one-sweep 3D pass runs beside the two-sweep one
 };
 
 // Launch helpers implemented in kernels_generic.cu.  Each returns the CUDA
@@ -185,7 +191,12 @@ struct Plane3dMaps {
     CUtensorMap u[2], ulo[2], f, wx, wy, wz, invd;
 };
 cudaError_t plane3d_encode(int prec, bool vark, const GridGeo &g, const IterBufs &b,
-                           Plane3dMaps *m);
+                           Plane3dMaps *m, bool two_sweep = false);
+// Two sweeps per pass (kernels_plane3d.cu): the passes of a cycle that do two
+// sweeps; the one-sweep pass (tail_only) does the rest.  Maps encoded with
+// two_sweep = true.
+Plane3dPlan plane3d2_plan(int prec, const GridGeo &g, bool vark, int num_sms);
+cudaError_t plane3d2_prepare(int prec, bool vark);
 GenericPlan generic_plan(int prec, const GridGeo &g, bool vark);
 int generic_partials_needed(const GridGeo &g);
 // maps: the handle's tensor maps, required when the plan is the 3D

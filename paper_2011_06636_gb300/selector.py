@@ -98,6 +98,66 @@ def collect(problem, seed, max_cycles=160, tol=1e-8, records=None, greedy=0.5):
     return X, y
 
 
+def rollout_collect(problem, seed, explore=0.3, max_cycles=200, tol=1e-8, horizon=1e-2):
+    """States along Alg. 1 trajectories on `problem` (dict n, eps, f), with a
+    random move instead of Alg. 1's one with probability `explore` so that
+    other states are visited too.  Each state is labelled with the move after
+    which Alg. 1 reduces the residual by `horizon` in the fewest sweeps (a
+    rollout per move: a library solve from the state whose first cycle runs at
+    the tried level and whose later cycles follow Alg. 1), i.e. one step of
+    policy improvement over Alg. 1; ties go to Alg. 1's own move.  Returns
+    (X, y, number of states where the label differs from Alg. 1's move)."""
+    import torch
+
+    from . import srj
+    n = problem["n"]
+    f = torch.as_tensor(np.ascontiguousarray(problem["f"]), device="cuda")
+    npts = int(np.prod(n))
+    handles = {}
+
+    def handle(level0):
+        if level0 not in handles:
+            handles[level0] = srj.srj_create(n, eps=problem.get("eps"),
+                                             precision=srj.SRJ_PREC_F64, level0=level0,
+                                             trace_capacity=8)
+        return handles[level0]
+
+    rng = np.random.default_rng(seed)
+    X, y, differ = [], [], 0
+    try:
+        h0 = handle(0)
+        u = torch.zeros_like(f)
+        r0 = srj.srj_residual_norm(h0, f.data_ptr(), u.data_ptr())
+        rn = srj.srj_run_levels(h0, f.data_ptr(), u.data_ptr(), [0])[0]
+        hist = [_log_ratio(rn / r0)]
+        level = 0
+        for _ in range(max_cycles):
+            if rn / r0 < tol:
+                break
+            ratio = math.exp(hist[0])
+            alg1 = min(24, level + 1) if ratio > 0.4 else (
+                max(0, level - 1) if 0.2 < ratio < 0.4 else level)
+            cands = [c for c in (level - 1, level, level + 1) if 0 <= c <= 24]
+            cost = {}
+            for c in cands:
+                uc = u.clone()
+                st = srj.srj_solve(handle(c), f.data_ptr(), uc.data_ptr(), horizon)
+                cost[c] = st["sweeps"] if st["status"] == srj.SRJ_OK else 10 ** 9
+            best = min(cands, key=lambda c: (cost[c], c != alg1))
+            differ += int(best != alg1)
+            X.append(features(hist, npts, len(n), level))
+            y.append(best)
+            nxt = alg1 if rng.random() >= explore else cands[int(rng.integers(len(cands)))]
+            rnew = srj.srj_run_levels(h0, f.data_ptr(), u.data_ptr(), [nxt])[0]
+            hist = [_log_ratio(rnew / rn)] + hist
+            rn = rnew
+            level = nxt
+    finally:
+        for hh in handles.values():
+            srj.srj_destroy(hh)
+    return X, y, differ
+
+
 def training_problems(seed=0):
     """Seeded 1D and 2D Poisson problems (b = 1 as in Sec. 3 and random f)."""
     from . import inputs
@@ -147,6 +207,108 @@ def analyse(records, n_set=200):
             "winners": winners}
 
 
+# ------------------------------------------------ Sec. 3, the paper's study
+# The matrix sizes of the paper's data collection (Sec. 3): 1D Poisson, b = 1,
+# x0 = 0, trials until ||r||_2 < 1e-8, about one million data points per size.
+SEC3_N = (2, 5, 10, 20, 30, 40, 50, 60, 70, 80, 90, 100, 200, 300, 400)
+SEC3_JSON = os.path.join(HERE, "sec3_thresholds.json")
+
+
+def sec3_collect(n, target=1_000_000, seed=0, tol=1e-8, max_steps=4000, mem_bytes=2 << 30):
+    """Records of the Sec. 3 collection on the size-n system (library
+    kernel, one trial per CTA), in batches of trials until at least `target`
+    records.  Returns (records as a numpy structured array, number of trials,
+    number of trials cut at max_steps)."""
+    import torch
+
+    from . import srj
+    dt = np.dtype(srj.MOVE_RECORD_DTYPE)
+    per_trial = 3 * max_steps
+    cap = max(1, mem_bytes // (per_trial * dt.itemsize))
+    parts, total, trial0, cut = [], 0, 0, 0
+    est = None  # records per trial seen so far
+    while total < target:
+        left = target - total
+        ntr = 256 if est is None else int(min(cap, max(64, 1.2 * left / est + 1)))
+        out = torch.empty(ntr * per_trial * dt.itemsize // 8, dtype=torch.float64, device="cuda")
+        counts = torch.zeros(ntr, dtype=torch.int32, device="cuda")
+        srj.srj_collect_moves(n, None, tol, 24, seed, trial0, ntr, max_steps, out.data_ptr(),
+                              counts.data_ptr())
+        # keep each trial's written records (device-side gather, then one copy)
+        rec = out.view(ntr, per_trial * dt.itemsize // 8)
+        words = dt.itemsize // 8
+        idx = torch.arange(per_trial, device="cuda")[None, :] < counts[:, None].long()
+        flat = rec.view(ntr, per_trial, words)[idx]
+        parts.append(flat.cpu().numpy().reshape(-1).view(dt))
+        c = counts.cpu().numpy()
+        cut += int(np.sum(c >= per_trial - 2))
+        total += int(c.sum())
+        trial0 += ntr
+        est = total / trial0
+    return np.concatenate(parts), trial0, cut
+
+
+def sec3_rates(rec):
+    """Average convergence rate of every record (Sec. 3, Eq.
+    average-convergence-rate): -log(r_after / r_before) / M of the tried level."""
+    m = np.asarray(LEVEL_M, dtype=np.float64)[rec["level"] + rec["action"]]
+    return -np.log(rec["r_after"] / rec["r_before"]) / m
+
+
+def alg1_action(ratio):
+    """Alg. 1's move for a previous residual ratio (the rule the study is
+    meant to recover): +1 above 0.4, -1 strictly between 0.2 and 0.4, else 0."""
+    return 1 if ratio > 0.4 else (-1 if 0.2 < ratio < 0.4 else 0)
+
+
+def sec3_study(sizes=SEC3_N, target=1_000_000, n_set=10000, seed=0):
+    """The paper's data collection on every size, post-processed together
+    (Sec. 3): per level, clusters of n_set records sorted by previous ratio,
+    the winning move of each cluster with non-overlapping 95 % intervals.
+    Returns a summary with the winners and how well Alg. 1's thresholds
+    (0.2, 0.4) and the best-fitting pair explain them."""
+    t0 = time.time()
+    allrec, per_size = [], {}
+    for n in sizes:
+        rec, trials, cut = sec3_collect(n, target=target, seed=seed + n)
+        allrec.append(rec)
+        per_size[str(n)] = {"records": int(len(rec)), "trials": trials, "trials_cut": cut,
+                            "max_level": int((rec["level"] + rec["action"]).max())}
+    rec = np.concatenate(allrec)
+    rows = np.stack([rec["prev_ratio"], rec["level"].astype(np.float64),
+                     rec["action"].astype(np.float64), sec3_rates(rec)], axis=1)
+    out = {"sizes": list(sizes), "records_total": int(len(rec)), "n_set": n_set,
+           "per_size": per_size}
+    out.update(sec3_summary(rows, n_set))
+    out["seconds"] = time.time() - t0
+    return out
+
+
+def sec3_summary(rows, n_set):
+    """Post-processing of Sec. 3 on rows (previous ratio, level, move, rate):
+    the cluster winners (analyse), the share of them Alg. 1's thresholds
+    (0.2, 0.4) explain, and the pair of thresholds (grid step 0.02) that
+    explains the most."""
+    res = analyse(rows, n_set=n_set)
+    win = res["winners"]
+    agree = sum(1 for r, _, a in win if alg1_action(r) == a)
+    best = (0, None, None)
+    grid = np.round(np.arange(0.02, 0.99, 0.02), 2)
+    for lo in grid:
+        for hi in grid[grid > lo]:
+            k = sum(1 for r, _, a in win
+                    if (1 if r > hi else (-1 if lo < r < hi else 0)) == a)
+            if k > best[0]:
+                best = (k, float(lo), float(hi))
+    return {"clusters_with_winner": res["clusters_with_winner"],
+            "keep_max_ratio": res["keep_max_ratio"], "down_ratio_range": res["down_ratio_range"],
+            "up_min_ratio": res["up_min_ratio"],
+            "alg1_agreement": agree / len(win) if win else None,
+            "best_fit_thresholds": {"low": best[1], "high": best[2],
+                                    "agreement": best[0] / len(win) if win else None},
+            "winners": [{"mean_ratio": r, "level": lv, "action": a} for r, lv, a in win]}
+
+
 def train(X, y, epochs=40, batch=64, lr=3e-3, seed=0):
     import torch
 
@@ -184,12 +346,30 @@ def main():
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--seeds", type=int, default=3)
     ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--labels", choices=["greedy", "rollout"], default="rollout",
+                    help="training labels: best next-cycle rate, or the move after which "
+                         "Alg. 1 reaches a 1e-2 reduction in the fewest sweeps")
+    ap.add_argument("--sec3", action="store_true",
+                    help="run the paper's Sec. 3 data collection and post-processing instead")
+    ap.add_argument("--sec3-target", type=int, default=1_000_000,
+                    help="records per matrix size (the paper: about one million)")
     args = ap.parse_args()
+    if args.sec3:
+        out = sec3_study(target=args.sec3_target)
+        with open(SEC3_JSON, "w") as fh:
+            json.dump(out, fh, indent=1)
+        print(json.dumps({k: v for k, v in out.items() if k != "winners"}))
+        return
     t0 = time.time()
     X, y, records = [], [], []
+    differ = 0
     for s in range(args.seeds):
         for i, p in enumerate(training_problems(seed=100 * s)):
-            a, b = collect(p, seed=1000 * s + i, records=records)
+            if args.labels == "rollout":
+                a, b, d = rollout_collect(p, seed=1000 * s + i)
+                differ += d
+            else:
+                a, b = collect(p, seed=1000 * s + i, records=records)
             X += a
             y += b
     t1 = time.time()
@@ -203,7 +383,12 @@ def main():
             "loss_first": float(loss[:50].mean()), "loss_last": float(loss[-50:].mean()),
             "train_accuracy": acc, "epochs": args.epochs,
             "label_counts": np.bincount(np.asarray(y), minlength=25).tolist(),
-            "sec3_postprocessing": {k: v for k, v in analyse(records).items() if k != "winners"}}
+            "labels": args.labels}
+    if args.labels == "rollout":
+        info["labels_differing_from_alg1"] = differ
+    else:
+        info["sec3_postprocessing"] = {k: v for k, v in analyse(records).items()
+                                       if k != "winners"}
     with open(os.path.splitext(args.out)[0] + ".json", "w") as fh:
         json.dump(info, fh, indent=1)
     print(json.dumps(info))

@@ -17,7 +17,7 @@ SRJ_OK, SRJ_EINVAL, SRJ_ENOMEM, SRJ_ECUDA, SRJ_ENOTCONV, SRJ_EDIVERGED, SRJ_ETIM
     SRJ_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["SRJ_OK", "SRJ_EINVAL", "SRJ_ENOMEM", "SRJ_ECUDA", "SRJ_ENOTCONV",
                 "SRJ_EDIVERGED", "SRJ_ETIMEOUT", "SRJ_EUNSUPPORTED"]
-SRJ_SEL_HEURISTIC, SRJ_SEL_INCREASING, SRJ_SEL_FIXED, SRJ_SEL_MLP = range(4)
+SRJ_SEL_HEURISTIC, SRJ_SEL_INCREASING, SRJ_SEL_FIXED, SRJ_SEL_MLP, SRJ_SEL_JACOBI = range(5)
 SRJ_PREC_F64, SRJ_PREC_F32, SRJ_PREC_MIXED = range(3)
 SRJ_TOL_REL, SRJ_TOL_ABS, SRJ_TOL_DINF = range(3)
 SRJ_BC_DIRICHLET, SRJ_BC_NEUMANN = range(2)
@@ -27,7 +27,17 @@ EXPORTS = ["srj_version", "srj_level_m", "srj_scheme_omegas", "srj_create", "srj
            "srj_solve_host", "srj_run_levels", "srj_residual_norm", "srj_get_trace",
            "srj_create_batched", "srj_solve_batched", "srj_mlp_set_weights", "srj_mlp_forward",
            "srj_mlp_train", "srj_residual_norm_noalloc", "srj_mg_create", "srj_mg_solve",
-           "srj_set_wait_limit", "srj_last_error", "srj_destroy"]
+           "srj_collect_moves", "srj_set_wait_limit", "srj_last_error", "srj_destroy"]
+
+
+class srj_move_record(C.Structure):
+    _fields_ = [("prev_ratio", C.c_double), ("r_before", C.c_double), ("r_after", C.c_double),
+                ("level", C.c_int32), ("action", C.c_int32)]
+
+
+# numpy view of an array of srj_move_record (same layout)
+MOVE_RECORD_DTYPE = [("prev_ratio", "<f8"), ("r_before", "<f8"), ("r_after", "<f8"),
+                     ("level", "<i4"), ("action", "<i4")]
 
 
 class srj_grid(C.Structure):
@@ -120,6 +130,10 @@ def load(build_if_missing: bool = True):
     L.srj_mg_create.restype = C.c_int
     L.srj_mg_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(srj_stats)]
     L.srj_mg_solve.restype = C.c_int
+    L.srj_collect_moves.argtypes = [C.c_int64, C.c_void_p, C.c_double, C.c_int32, C.c_uint64,
+                                    C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]
+    L.srj_collect_moves.restype = C.c_int
     L.srj_set_wait_limit.argtypes = [H, C.c_int64]
     L.srj_set_wait_limit.restype = C.c_int
     L.srj_destroy.argtypes = [H]
@@ -304,6 +318,17 @@ def srj_mlp_train(x_ptr, y_ptr, n, order_ptr, steps, batch, lr, theta_ptr, strea
     if rc != SRJ_OK:
         raise SrjError(rc, "srj_mlp_train")
     return loss[:steps]
+
+
+def srj_collect_moves(n, f_ptr, tol, max_level, seed, trial0, ntrials, max_steps, out_ptr,
+                      counts_ptr, stream=None):
+    """Sec. 3 data collection (see include/srj.h); out_ptr / counts_ptr are
+    caller-owned device buffers."""
+    rc = load().srj_collect_moves(int(n), f_ptr, float(tol), int(max_level), int(seed),
+                                  int(trial0), int(ntrials), int(max_steps), out_ptr, counts_ptr,
+                                  stream)
+    if rc != SRJ_OK:
+        raise SrjError(rc, "srj_collect_moves")
 
 
 def srj_set_wait_limit(h, polls):

@@ -65,7 +65,7 @@ def test_binding_structs_and_enums_match_header(tmp_path):
     from paper_2011_06636_gb300 import srj
     structs = {"srj_grid": srj.srj_grid, "srj_stencil": srj.srj_stencil,
                "srj_opts": srj.srj_opts, "srj_stats": srj.srj_stats,
-               "srj_mg_opts": srj.srj_mg_opts}
+               "srj_mg_opts": srj.srj_mg_opts, "srj_move_record": srj.srj_move_record}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "srj.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
@@ -73,7 +73,8 @@ def test_binding_structs_and_enums_match_header(tmp_path):
             lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
     enums = ["SRJ_TOL_REL", "SRJ_TOL_ABS", "SRJ_TOL_DINF", "SRJ_BC_DIRICHLET", "SRJ_BC_NEUMANN",
              "SRJ_PREC_F64", "SRJ_PREC_F32", "SRJ_PREC_MIXED", "SRJ_SEL_HEURISTIC",
-             "SRJ_SEL_INCREASING", "SRJ_SEL_FIXED", "SRJ_SEL_MLP", "SRJ_EUNSUPPORTED"]
+             "SRJ_SEL_INCREASING", "SRJ_SEL_FIXED", "SRJ_SEL_MLP", "SRJ_SEL_JACOBI",
+             "SRJ_EUNSUPPORTED"]
     for e in enums:
         lines.append('printf("%s %%d\\n", (int)%s);' % (e, e))
     lines.append("return 0; }")

@@ -574,3 +574,79 @@ def test_one_cta_solve_matches_pass_kernels(S, orc, n, prec, kind, monkeypatch):
         # the inner FP32-pair sweeps round differently in the two kernels;
         # both solutions meet the same FP64 residual tolerance
         np.testing.assert_allclose(u1, u2, rtol=0, atol=1e-6 * scale)
+
+
+# -------------------------------------- 3D passes with two sweeps per pass
+# Ragged in every direction, several 32 x 16 tiles and z chunks (16 planes
+# and a shorter last one), constant and variable coefficients.
+P3D2_CASES = [("70x19x75", [70, 19, 75], None), ("45x33x70_vark", [45, 33, 70], "vark"),
+              ("64x50x12", [64, 50, 12], None), ("33x40x37_vark", [33, 40, 37], "vark")]
+
+
+@pytest.mark.parametrize("name,n,kind", P3D2_CASES, ids=[c[0] for c in P3D2_CASES])
+def test_plane3d_two_sweeps_f64_fixed_schedule(S, orc, name, n, kind):
+    """FP64 two-sweep 3D passes (temporal depth 2) element by element against
+    the oracle; levels with odd and even M, so cycles end both with a single
+    sweep and with a pair."""
+    f = inputs.uniform_rhs(n, seed=51).ravel()
+    k = inputs.lognormal_k(n, seed=3, corr=4.0) if kind else None
+    eps = [1.0, 0.7, 1.3] if kind else None
+    levels = [0, 1, 2, 3, 4, 5, 8, 11, 9, 12]
+    h, kt = make(S, n, S.SRJ_PREC_F64, eps=eps, k=k, temporal_depth=2)
+    fd, ud = dev(f), dev(np.zeros(f.size))
+    try:
+        rn = S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    P = orc.Problem(n, eps=eps, k=k)
+    uo, rno = orc.run_levels(P, f, np.zeros(f.size), levels)
+    r0 = orc.residual_norm(P, np.zeros(f.size), f)
+    assert np.max(np.abs(ug - uo)) <= 1e-10 * np.max(np.abs(uo))
+    assert np.all(np.abs(rn - rno) <= 1e-10 * rno + 1e-13 * r0)
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+@pytest.mark.parametrize("name,n,kind", P3D2_CASES, ids=[c[0] for c in P3D2_CASES])
+def test_plane3d_two_sweeps_mixed_solve(S, orc, name, n, kind, depth):
+    """The mixed-precision solve with two-sweep FP32-pair 3D passes against
+    the oracle's FP64 solve: both meet rel 1e-8 (the library's residual
+    recomputed by the oracle), and the two solutions lie within
+    (||r_gpu|| + ||r_oracle||) / lambda_min of each other, lambda_min bounded
+    below by min(k) times the constant operator's."""
+    f = inputs.uniform_rhs(n, seed=52).ravel()
+    k = inputs.lognormal_k(n, seed=3, corr=4.0) if kind else None
+    eps = [1.0, 0.7, 1.3] if kind else None
+    P = orc.Problem(n, eps=eps, k=k)
+    ref = orc.srj_solve(P, f, tol=1e-8)
+    h, kt = make(S, n, S.SRJ_PREC_MIXED, eps=eps, k=k, temporal_depth=depth)
+    fd, ud = dev(f), dev(np.zeros(f.size))
+    try:
+        st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-8)
+        ug = ud.cpu().numpy()
+    finally:
+        S.srj_destroy(h)
+    assert st["status"] == S.SRJ_OK, st
+    rn_true = orc.residual_norm(P, ug, f)
+    assert rn_true / ref["r0"] < 1e-8
+    lam = lam_min_const(n, eps) * (float(np.min(k)) if k is not None else 1.0)
+    assert np.linalg.norm(ug - ref["u"]) <= (rn_true + ref["rn"]) / lam * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("name,n,kind", P3D2_CASES[:2], ids=[c[0] for c in P3D2_CASES[:2]])
+def test_plane3d_two_sweeps_f32_within_bound(S, orc, name, n, kind):
+    f = inputs.uniform_rhs(n, seed=53).ravel()
+    k = inputs.lognormal_k(n, seed=3, corr=4.0) if kind else None
+    levels = [0, 1, 2, 3, 5, 7]
+    h, kt = make(S, n, S.SRJ_PREC_F32, k=k, temporal_depth=2)
+    fd, ud = dev(f, torch.float32), dev(np.zeros(f.size), torch.float32)
+    try:
+        S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
+        ug = ud.cpu().numpy().astype(np.float64)
+    finally:
+        S.srj_destroy(h)
+    f32 = f.astype(np.float32).astype(np.float64)
+    P = orc.Problem(n, k=k)
+    uo, _ = orc.run_levels(P, f32, np.zeros(f.size), levels)
+    bound = 8 * EPS32 * sum(S.srj_level_m(l) ** 3 for l in levels) * np.max(np.abs(uo))
+    assert np.max(np.abs(ug - uo)) <= bound

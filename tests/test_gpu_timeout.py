@@ -36,12 +36,15 @@ def _solve_raw(S, h, f, u, tol):
 GRID = [40, 24, 70]
 
 
+@pytest.mark.parametrize("depth", [0, 2])
 @pytest.mark.parametrize("prec", ["F64", "MIXED"])
-def test_wait_that_runs_out_ends_the_solve_cleanly(S, orc, prec):
+def test_wait_that_runs_out_ends_the_solve_cleanly(S, orc, prec, depth):
+    """depth 2: the graph runs the two-sweep pass and the one-sweep tail pass
+    side by side; the first pass (the initial residual, a tail pass) gives up."""
     p = getattr(S, "SRJ_PREC_" + prec)
     f_np = inputs.uniform_rhs(GRID, seed=31).ravel()
     f = torch.as_tensor(f_np, device="cuda")
-    h = S.srj_create(GRID, precision=p)
+    h = S.srj_create(GRID, precision=p, temporal_depth=depth)
     try:
         for _ in range(2):  # two timed-out solves in a row
             S.srj_set_wait_limit(h, 0)
