@@ -61,26 +61,35 @@ KERNEL_SOURCES = ["paper_2011_06636_gb300/csrc/" + f for f in (
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "wave2d_fp32pair_T2_4096.md")
 
 
-def kernel_source_hash():
+# the same for the 3D mixed solve's pass (captured at 256^3: its traffic is
+# scaled to the bench's grid by the points of a launch)
+KERNEL_SOURCES_3D = ["paper_2011_06636_gb300/csrc/" + f for f in (
+    "kernels_plane3d.cu", "df32.cuh", "stencil_point.cuh", "pass_common.cuh", "mlp.cuh",
+    "srj_internal.h")]
+PROFILE_SUMMARY_3D = os.path.join(ROOT, "profiles", "plane3d2_fp32pair_vark_256.md")
+PROFILE_POINTS_3D = 256 ** 3
+
+
+def kernel_source_hash(sources=KERNEL_SOURCES):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when it is absent or the kernel changed since."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def profiled_traffic(summary=PROFILE_SUMMARY, sources=KERNEL_SOURCES):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, or
+    None when it is absent or the kernel's sources changed since."""
+    if not os.path.exists(summary):
         return None
     vals = {}
-    for line in open(PROFILE_SUMMARY):
+    for line in open(summary):
         if ":" in line and line.strip().startswith(("dram_bytes_per_launch", "source_sha256")):
             k, v = line.strip().split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source_sha256") != kernel_source_hash():
+    if vals.get("source_sha256") != kernel_source_hash(sources):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -495,21 +504,27 @@ def vark3d_leg(srj, inputs, torch, stream, seed=0, side=512, fp64=True, depth=0)
                       "rel_residual": st["rn"] / st["r0"],
                       "status": srj.STATUS_NAMES[st["status"]]}
         if label == "mixed":
-            # roofline of the inner pass (plane3d_kernel, one sweep per pass):
-            # algorithmic 16 B per update (read u, r, k; write u, FP32), over
-            # the device time of the inner cycle loops; the FP32-pair design
-            # moves 36 B (iterate hi/lo read and write 16, rhs 4, three face
-            # weights and 1/D 16)
+            # roofline of the inner passes (plane3d2_kernel, two sweeps per
+            # pass): algorithmic 16 B per update (read u, r, k; write u,
+            # FP32), over the device time of the inner cycle loops; the
+            # FP32-pair design moves 36 B per point and pass (iterate hi/lo
+            # read and write 16, rhs 4, three face weights and 1/D 16), 18 B
+            # per update with two sweeps per pass
             hbm_peak, peak_kind = peaks()
             inner_s = st["inner_seconds"]
             ach = ALGO_BYTES_PER_POINT_VARK * st["sweeps"] * f.numel() / inner_s / 1e9
             res[label]["inner_seconds"] = inner_s
+            tr = profiled_traffic(PROFILE_SUMMARY_3D, KERNEL_SOURCES_3D)
             res[label]["roofline"] = {
                 "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "kernel": "plane3d_kernel<FP32-pair, variable k>",
+                "frac": ach / hbm_peak,
+                "traffic": tr * f.numel() / PROFILE_POINTS_3D if tr else None,
+                "traffic_note": "ncu DRAM bytes of one two-sweep launch at 256^3, scaled to "
+                                "this grid by its points",
+                "kernel": "plane3d2_kernel<FP32-pair, variable k> (two sweeps per pass)",
                 "algorithmic_bytes_per_update": ALGO_BYTES_PER_POINT_VARK,
-                "bytes_moved_per_update_by_design": 36.0,
-                "design_bytes_frac": 36.0 * st["sweeps"] * f.numel() / inner_s / 1e9 / hbm_peak,
+                "bytes_moved_per_update_by_design": 18.0,
+                "design_bytes_frac": 18.0 * st["sweeps"] * f.numel() / inner_s / 1e9 / hbm_peak,
                 "timing": "CUDA events around the inner cycle loops",
                 "peak_kind": peak_kind}
         sols[label] = u

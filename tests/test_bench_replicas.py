@@ -45,17 +45,19 @@ def test_two_gloo_ranks_aggregate_replicas():
         assert value == pytest.approx(15.0)
 
 
-def test_profiled_traffic_reads_only_a_matching_summary(tmp_path, monkeypatch):
-    # the DRAM traffic of the dominant kernel is reported from the committed
-    # ncu summary only while the kernel sources hash to the recorded value
+def test_profiled_traffic_reads_only_a_matching_summary(tmp_path):
+    # the DRAM traffic of a kernel is reported from its committed ncu summary
+    # only while the kernel's sources hash to the recorded value
     import bench
-    good = tmp_path / "good.md"
-    good.write_text("dram_bytes_per_launch: 1234\nsource_sha256: `%s`\n" % bench.kernel_source_hash())
-    stale = tmp_path / "stale.md"
-    stale.write_text("dram_bytes_per_launch: 1234\nsource_sha256: `%s`\n" % ("0" * 64))
-    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(good))
-    assert bench.profiled_traffic() == 1234
-    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(stale))
-    assert bench.profiled_traffic() is None
-    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(tmp_path / "missing.md"))
-    assert bench.profiled_traffic() is None
+    for sources in (bench.KERNEL_SOURCES, bench.KERNEL_SOURCES_3D):
+        good = tmp_path / "good.md"
+        good.write_text("dram_bytes_per_launch: 1234\nsource_sha256: `%s`\n"
+                        % bench.kernel_source_hash(sources))
+        stale = tmp_path / "stale.md"
+        stale.write_text("dram_bytes_per_launch: 1234\nsource_sha256: `%s`\n" % ("0" * 64))
+        assert bench.profiled_traffic(str(good), sources) == 1234
+        assert bench.profiled_traffic(str(stale), sources) is None
+        assert bench.profiled_traffic(str(tmp_path / "missing.md"), sources) is None
+    # the two kernels' source lists hash differently
+    assert bench.kernel_source_hash(bench.KERNEL_SOURCES) != bench.kernel_source_hash(
+        bench.KERNEL_SOURCES_3D)
