@@ -91,13 +91,16 @@ struct BatchData {
     BatchProb *dprobs = nullptr;
     BatchState *dstates = nullptr;
     BatchState *hstates = nullptr;  // pinned
-    int32_t *item_prob = nullptr;
+    int32_t *item_prob[kBatchLayouts] = {};
     double *partials = nullptr;
-    int items_cap = 0;
+    int items_cap[kBatchLayouts] = {};
     unsigned int *ndone = nullptr;
+    int32_t *ctl = nullptr;        // layout of the running launch, CTAs done with it
+    long long *active = nullptr;   // items of the unfinished problems, per layout
+    int partials_cap = 0;
     float *arena = nullptr;  // all inner buffers: per problem r32, hi0, hi1, lo0, lo1
     size_t arena_floats = 0;
-    int T = 4, R = 64, total_items = 0;
+    int T = 4, R = 64, total_items[kBatchLayouts] = {};
     bool tuned = false;
     double graph_tol = -1.0;
     cudaGraph_t graph = nullptr;
@@ -529,37 +532,58 @@ srj_status solve_mixed(srj_handle *h, const double *f, double *u, double tol, sr
 srj_status batch_layout(srj_handle *h, int T, int R) {
     BatchData *B = h->batch;
     const int outw = batched_outw(T);
-    std::vector<int32_t> owner;
-    int base = 0;
+    // segment heights of the layouts: the tuned one, then a quarter and an
+    // eighth of it (at least 4 rows)
+    int Rl[kBatchLayouts] = {R, R / 4, R / 8};
+    for (int l = 1; l < kBatchLayouts; ++l)
+        if (Rl[l] < 4) Rl[l] = 4;
+    std::vector<int32_t> owner[kBatchLayouts];
+    int base[kBatchLayouts] = {};
     for (int p = 0; p < B->nprob; ++p) {
         BatchProb &P = B->probs[p];
         P.nstrips = (P.geo.nx + outw - 1) / outw;
-        P.R = R < P.geo.ny ? R : P.geo.ny;
-        P.nsegs = (P.geo.ny + P.R - 1) / P.R;
-        P.nitems = P.nstrips * P.nsegs;
-        P.item_base = base;
-        for (int i = 0; i < P.nitems; ++i) owner.push_back(p);
-        base += P.nitems;
+        for (int l = 0; l < kBatchLayouts; ++l) {
+            P.R[l] = Rl[l] < P.geo.ny ? Rl[l] : P.geo.ny;
+            P.nsegs[l] = (P.geo.ny + P.R[l] - 1) / P.R[l];
+            P.nitems[l] = P.nstrips * P.nsegs[l];
+            P.item_base[l] = base[l];
+            for (int i = 0; i < P.nitems[l]; ++i) owner[l].push_back(p);
+            base[l] += P.nitems[l];
+        }
     }
-    B->total_items = base;
     B->T = T;
     B->R = R;
-    if (base > B->items_cap) {
-        dfree(B->item_prob);
-        dfree(B->partials);
-        B->item_prob = nullptr;
-        B->partials = nullptr;
-        if (dalloc(&B->item_prob, (size_t)base * sizeof(int32_t)) != cudaSuccess ||
-            dalloc(&B->partials, (size_t)base * sizeof(double)) != cudaSuccess)
-            return fail(h, SRJ_ENOMEM, "batched item tables");
-        B->items_cap = base;
+    int most = 0;
+    for (int l = 0; l < kBatchLayouts; ++l) {
+        B->total_items[l] = base[l];
+        if (base[l] > most) most = base[l];
+        if (base[l] > B->items_cap[l]) {
+            dfree(B->item_prob[l]);
+            B->item_prob[l] = nullptr;
+            if (dalloc(&B->item_prob[l], (size_t)base[l] * sizeof(int32_t)) != cudaSuccess)
+                return fail(h, SRJ_ENOMEM, "batched item tables");
+            B->items_cap[l] = base[l];
+        }
+        CK(cudaMemcpyAsync(B->item_prob[l], owner[l].data(), (size_t)base[l] * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, h->stream));
     }
-    CK(cudaMemcpyAsync(B->item_prob, owner.data(), (size_t)base * sizeof(int32_t),
-                       cudaMemcpyHostToDevice, h->stream));
+    if (most > B->partials_cap) {
+        dfree(B->partials);
+        B->partials = nullptr;
+        if (dalloc(&B->partials, (size_t)most * sizeof(double)) != cudaSuccess)
+            return fail(h, SRJ_ENOMEM, "batched partials");
+        B->partials_cap = most;
+    }
     CK(cudaMemcpyAsync(B->dprobs, B->probs.data(), B->probs.size() * sizeof(BatchProb),
                        cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return SRJ_OK;
+}
+
+// Warps the batched grid keeps resident (the layout choice compares item
+// counts against it).
+int batch_resident_warps(srj_handle *h) {
+    return batched_grid(h->batch->T, h->num_sms) * (h->batch->T >= 4 ? 8 : 6);
 }
 
 BatchLaunch batch_args(srj_handle *h, double tol, bool tuning) {
@@ -567,11 +591,17 @@ BatchLaunch batch_args(srj_handle *h, double tol, bool tuning) {
     BatchLaunch b{};
     b.probs = B->dprobs;
     b.states = B->dstates;
-    b.item_prob = B->item_prob;
+    for (int l = 0; l < kBatchLayouts; ++l) {
+        b.item_prob[l] = B->item_prob[l];
+        b.total_items[l] = B->total_items[l];
+    }
+    b.ctl = B->ctl;
+    b.active = B->active;
+    b.resident_warps = batch_resident_warps(h);
+    b.fixed_layout = tuning ? 0 : -1;
     b.partials = B->partials;
     b.ndone = B->ndone;
     b.nprob = B->nprob;
-    b.total_items = B->total_items;
     b.w64 = h->w64;
     for (int l = 0; l < kNumLevels; ++l) {
         b.lvl_m[l] = kLevelM[l];
@@ -603,6 +633,16 @@ srj_status batch_reset(srj_handle *h) {
     CK(cudaMemcpyAsync(B->dstates, B->hstates, (size_t)B->nprob * sizeof(BatchState),
                        cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemsetAsync(B->ndone, 0, sizeof(unsigned int), h->stream));
+    // every problem active: the first launch takes the tallest layout whose
+    // items cover the resident warps
+    long long act[kBatchLayouts];
+    int32_t ctl[2] = {kBatchLayouts - 1, 0};
+    for (int l = 0; l < kBatchLayouts; ++l) act[l] = B->total_items[l];
+    for (int l = kBatchLayouts - 1; l >= 0; --l)
+        if (act[l] >= batch_resident_warps(h)) ctl[0] = l;
+    CK(cudaMemcpyAsync(B->active, act, sizeof(act), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(B->ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     CK(cudaMemsetAsync(B->arena, 0, B->arena_floats * sizeof(float), h->stream));
     return SRJ_OK;
 }
@@ -1144,6 +1184,8 @@ srj_status srj_create_batched(int32_t nprob, const srj_grid *grids, const srj_st
         dalloc(&B->dprobs, (size_t)nprob * sizeof(BatchProb)) != cudaSuccess ||
         dalloc(&B->dstates, (size_t)nprob * sizeof(BatchState)) != cudaSuccess ||
         dalloc(&B->ndone, sizeof(unsigned int)) != cudaSuccess ||
+        dalloc(&B->ctl, 2 * sizeof(int32_t)) != cudaSuccess ||
+        dalloc(&B->active, kBatchLayouts * sizeof(long long)) != cudaSuccess ||
         halloc(&B->hstates, (size_t)nprob * sizeof(BatchState)) != cudaSuccess) {
         srj_destroy(h);
         return SRJ_ENOMEM;
@@ -1485,9 +1527,10 @@ srj_status srj_destroy(srj_handle *h) {
     if (BatchData *B = h->batch) {
         if (B->exec) cudaGraphExecDestroy(B->exec);
         if (B->graph) cudaGraphDestroy(B->graph);
-        for (void *p : {(void *)B->dprobs, (void *)B->dstates, (void *)B->item_prob,
-                        (void *)B->partials, (void *)B->ndone, (void *)B->arena})
+        for (void *p : {(void *)B->dprobs, (void *)B->dstates, (void *)B->partials,
+                        (void *)B->ndone, (void *)B->arena, (void *)B->ctl, (void *)B->active})
             dfree(p);
+        for (int l = 0; l < kBatchLayouts; ++l) dfree(B->item_prob[l]);
         if (B->hstates) cudaFreeHost(B->hstates);
         delete B;
     }

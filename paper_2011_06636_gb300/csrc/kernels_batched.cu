@@ -142,7 +142,14 @@ __device__ void finalize_problem(const BatchLaunch &b, int p, const PassPlan &pl
         S.outer += 1;
         S.phase = BPH_OUTER;
     }
-    if (done) S.phase = BPH_DONE;
+    if (done) {
+        S.phase = BPH_DONE;
+        // its items leave the counts that choose the next launches' layout
+        const BatchProb &P = b.probs[p];
+        for (int l = 0; l < kBatchLayouts; ++l)
+            atomicAdd((unsigned long long *)&b.active[l],
+                      (unsigned long long)(-(long long)P.nitems[l]));
+    }
     S.ticket = 0;
     __threadfence();
     if (done) {
@@ -165,17 +172,20 @@ __global__ void __launch_bounds__(32 * batch_warps<T>(), (batch_min_blocks<T>())
     unsigned char *wbase = smem + warp * W::SMEM_WARP;
     const int gwarp = blockIdx.x * kBW + warp;
     const int nwarps = gridDim.x * kBW;
+    // this launch's layout: written only by the previous launch's last CTA
+    const int lay = b.fixed_layout >= 0 ? b.fixed_layout : *(volatile const int32_t *)b.ctl;
+    const int32_t *item_prob = b.item_prob[lay];
 
-    for (int item = gwarp; item < b.total_items; item += nwarps) {
-        const int p = b.item_prob[item];
+    for (int item = gwarp; item < b.total_items[lay]; item += nwarps) {
+        const int p = item_prob[item];
         const BatchProb &P = b.probs[p];
         BatchState &S = b.states[p];
         const int phase = S.phase;  // uniform: same address for every lane
         if (phase == BPH_DONE) continue;
-        const int li = item - P.item_base;
+        const int li = item - P.item_base[lay];
         const int strip = li % P.nstrips, seg = li / P.nstrips;
-        const int y0 = seg * P.R;
-        const int y1 = min(y0 + P.R, P.geo.ny);
+        const int y0 = seg * P.R[lay];
+        const int y1 = min(y0 + P.R[lay], P.geo.ny);
         const int x0 = strip * W::OUTW;
         const int x1 = min(x0 + W::OUTW, P.geo.nx);
         PassPlan plan{};
@@ -197,20 +207,41 @@ __global__ void __launch_bounds__(32 * batch_warps<T>(), (batch_min_blocks<T>())
         if (lane == 0) {
             b.partials[item] = part;
             __threadfence();
-            last = atomicAdd(&S.ticket, 1u) == (unsigned int)(P.nitems - 1);
+            last = atomicAdd(&S.ticket, 1u) == (unsigned int)(P.nitems[lay] - 1);
         }
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last) {
             __threadfence();
             double acc = 0.0;
-            const volatile double *pv = b.partials + P.item_base;
-            for (int i = lane; i < P.nitems; i += 32) acc += pv[i];
+            const volatile double *pv = b.partials + P.item_base[lay];
+            for (int i = lane; i < P.nitems[lay]; i += 32) acc += pv[i];
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             int pick = -1;
             if (phase == BPH_INNER) pick = mlp_pick_at_cycle_end(&S.in, b.cfg, plan, acc, b.lvl_m, lane);
             if (lane == 0) finalize_problem(b, p, plan, acc, pick);
         }
         __syncwarp();
+    }
+    // the launch's last CTA picks the next launch's layout: the tallest
+    // segments whose items still cover the resident warps, else the shortest
+    __syncthreads();
+    if (threadIdx.x == 0 && b.fixed_layout < 0) {
+        __threadfence();
+        if (atomicAdd((unsigned int *)&b.ctl[1], 1u) == gridDim.x - 1) {
+            __threadfence();
+            int next = kBatchLayouts - 1;
+            for (int l = 0; l < kBatchLayouts; ++l) {
+                const long long act =
+                    (long long)atomicAdd((unsigned long long *)&b.active[l], 0ull);
+                if (act >= b.resident_warps) {
+                    next = l;
+                    break;
+                }
+            }
+            b.ctl[0] = next;
+            b.ctl[1] = 0;
+            __threadfence();
+        }
     }
 }
 

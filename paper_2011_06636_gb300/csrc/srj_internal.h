@@ -28,6 +28,7 @@ constexpr int kNumLevels = 25;
 // are then still drained with this limit.
 constexpr long long kDefaultWaitLimit = 1LL << 22;
 constexpr int kTotalOmegas = 9710;  // sum of M over the 25 levels
+constexpr int kBatchLayouts = 3;    // item layouts of the batched solve
 // The factor tables end with kJacobiOnes factors omega = 1 (at offset
 // kTotalOmegas): every pass of a plain-Jacobi solve reads its factors there.
 constexpr int kJacobiOnes = 8;
@@ -226,13 +227,20 @@ cudaError_t wave2d_launch(const Wave2dPlan &p, const PassLaunch &a, cudaStream_t
 cudaError_t add_wave2d_node(const Wave2dPlan &p, const PassLaunch &a, cudaGraph_t body);
 
 // Batched persistent solve of many 2D constant-coefficient problems
-// (kernels_batched.cu).  Per problem: immutable geometry and buffers ...
+// (kernels_batched.cu).  The problems are cut into items (strip x row segment)
+// in kBatchLayouts layouts of decreasing segment height; each launch uses one
+// layout for every problem, chosen at the end of the previous launch from the
+// items the unfinished problems have (tall segments while the problems fill
+// the GPU, short ones once a few large problems remain and the length of an
+// item sets the time of a pass).  Per problem: immutable geometry and buffers ...
 struct BatchProb {
     GridGeo geo;
     IterBufs inner;   // f = FP32 inner rhs, u[2] / ulo[2] = FP32-pair iterates (padded)
     const double *f;  // user arrays (dense FP64), set per solve
     double *u;
-    int nstrips, nsegs, R, nitems, item_base;
+    // item decomposition of each layout (segment heights R, largest first)
+    int nstrips;
+    int nsegs[kBatchLayouts], R[kBatchLayouts], nitems[kBatchLayouts], item_base[kBatchLayouts];
 };
 // ... and a state machine OUTER -> INNER -> UPDATE -> OUTER ... -> DONE.
 struct BatchState {
@@ -245,10 +253,16 @@ struct BatchState {
 struct BatchLaunch {
     const BatchProb *probs;
     BatchState *states;
-    const int32_t *item_prob;  // problem of every item (problem-major order)
-    double *partials;          // one slot per item
+    const int32_t *item_prob[kBatchLayouts];  // problem of every item (problem-major order)
+    double *partials;          // one slot per item (of the largest layout)
     unsigned int *ndone;
-    int nprob, total_items;
+    int nprob, total_items[kBatchLayouts];
+    // layout choice: ctl[0] the layout of the running launch, ctl[1] the CTAs
+    // that finished it; active[l]: items of the unfinished problems in layout l
+    int32_t *ctl;
+    long long *active;
+    int resident_warps;  // warps the grid keeps resident
+    int fixed_layout;    // >= 0: every launch uses this layout (autotuning)
     const double *w64;
     int lvl_m[kNumLevels], lvl_off[kNumLevels];
     double tol, inner_tol;

@@ -98,7 +98,8 @@ def collect(problem, seed, max_cycles=160, tol=1e-8, records=None, greedy=0.5):
     return X, y
 
 
-def rollout_collect(problem, seed, explore=0.3, max_cycles=200, tol=1e-8, horizon=1e-2):
+def rollout_collect(problem, seed, explore=0.3, max_cycles=200, tol=1e-8, horizon=1e-2,
+                    deadline=None):
     """States along Alg. 1 trajectories on `problem` (dict n, eps, f), with a
     random move instead of Alg. 1's one with probability `explore` so that
     other states are visited too.  Each state is labelled with the move after
@@ -132,7 +133,7 @@ def rollout_collect(problem, seed, explore=0.3, max_cycles=200, tol=1e-8, horizo
         hist = [_log_ratio(rn / r0)]
         level = 0
         for _ in range(max_cycles):
-            if rn / r0 < tol:
+            if rn / r0 < tol or (deadline is not None and time.time() > deadline):
                 break
             ratio = math.exp(hist[0])
             alg1 = min(24, level + 1) if ratio > 0.4 else (
@@ -158,16 +159,21 @@ def rollout_collect(problem, seed, explore=0.3, max_cycles=200, tol=1e-8, horizo
     return X, y, differ
 
 
-def training_problems(seed=0):
-    """Seeded 1D and 2D Poisson problems (b = 1 as in Sec. 3 and random f)."""
+def training_problems(seed=0, small=False):
+    """Seeded 1D and 2D Poisson problems (b = 1 as in Sec. 3 and random f),
+    sizes interleaved; small=True keeps 1D up to 4096 points and 2D up to
+    256^2 (what the rollout labels can afford)."""
     from . import inputs
+    n1 = (16, 32, 64, 128, 256, 512, 1024, 2048, 4096) + (() if small else (8192, 16384))
+    n2 = (16, 32, 64, 128, 256) + (() if small else (512, 1024))
     probs = []
-    for N in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384):
-        probs.append({"n": [N], "f": np.ones(N)})
-        probs.append({"n": [N], "f": inputs.uniform_rhs([N], seed=seed + N).ravel()})
-    for s in (16, 32, 64, 128, 256, 512, 1024):
-        probs.append({"n": [s, s], "f": np.ones(s * s)})
-        probs.append({"n": [s, s], "f": inputs.uniform_rhs([s, s], seed=seed + s).ravel()})
+    for i in range(max(len(n1), len(n2))):
+        for N in ([n1[i]] if i < len(n1) else []):
+            probs.append({"n": [N], "f": np.ones(N)})
+            probs.append({"n": [N], "f": inputs.uniform_rhs([N], seed=seed + N).ravel()})
+        for s_ in ([n2[i]] if i < len(n2) else []):
+            probs.append({"n": [s_, s_], "f": np.ones(s_ * s_)})
+            probs.append({"n": [s_, s_], "f": inputs.uniform_rhs([s_, s_], seed=seed + s_).ravel()})
     return probs
 
 
@@ -349,6 +355,8 @@ def main():
     ap.add_argument("--labels", choices=["greedy", "rollout"], default="rollout",
                     help="training labels: best next-cycle rate, or the move after which "
                          "Alg. 1 reaches a 1e-2 reduction in the fewest sweeps")
+    ap.add_argument("--budget", type=float, default=900.0,
+                    help="seconds of trace collection for the rollout labels")
     ap.add_argument("--sec3", action="store_true",
                     help="run the paper's Sec. 3 data collection and post-processing instead")
     ap.add_argument("--sec3-target", type=int, default=1_000_000,
@@ -363,10 +371,13 @@ def main():
     t0 = time.time()
     X, y, records = [], [], []
     differ = 0
+    deadline = t0 + args.budget
     for s in range(args.seeds):
-        for i, p in enumerate(training_problems(seed=100 * s)):
+        for i, p in enumerate(training_problems(seed=100 * s, small=args.labels == "rollout")):
             if args.labels == "rollout":
-                a, b, d = rollout_collect(p, seed=1000 * s + i)
+                if time.time() > deadline:
+                    break
+                a, b, d = rollout_collect(p, seed=1000 * s + i, deadline=deadline)
                 differ += d
             else:
                 a, b = collect(p, seed=1000 * s + i, records=records)

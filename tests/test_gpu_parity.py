@@ -650,3 +650,48 @@ def test_plane3d_two_sweeps_f32_within_bound(S, orc, name, n, kind):
     uo, _ = orc.run_levels(P, f32, np.zeros(f.size), levels)
     bound = 8 * EPS32 * sum(S.srj_level_m(l) ** 3 for l in levels) * np.max(np.abs(uo))
     assert np.max(np.abs(ug - uo)) <= bound
+
+
+def test_batched_layout_switching_keeps_every_solution(S):
+    """A batch large enough that the first launches take the tallest row
+    segments and later ones, with only a few large problems left, the
+    shorter layouts: every problem reaches rel 1e-8 (FP64 residual
+    recomputed by torch), lies within the residual bound of its own
+    single-grid mixed solve (itself oracle-checked above), and a second solve
+    repeats every bit."""
+    probs = inputs.batched_problems(count=48, seed=9, smin=300, smax=900)
+    fs = [inputs.normal_rhs(p["n"], seed=p["seed_f"]).ravel() for p in probs]
+    ns = [p["n"] for p in probs]
+    eps = [p["eps"] for p in probs]
+    h = S.srj_create_batched(ns, eps=eps)
+    fd = [dev(f) for f in fs]
+    ud = [dev(np.zeros(f.size)) for f in fs]
+    ud2 = [dev(np.zeros(f.size)) for f in fs]
+    try:
+        rc, stats = S.srj_solve_batched(h, [t.data_ptr() for t in fd], [t.data_ptr() for t in ud], 1e-8)
+        rc2, _ = S.srj_solve_batched(h, [t.data_ptr() for t in fd], [t.data_ptr() for t in ud2], 1e-8)
+    finally:
+        S.srj_destroy(h)
+    assert rc == S.SRJ_OK and rc2 == S.SRJ_OK
+    assert all(torch.equal(a, b) for a, b in zip(ud, ud2))
+    for p, f, u, st in zip(probs, fd, ud, stats):
+        nx, ny = p["n"]
+        ex, ey = p["eps"] or [1.0, 1.0]
+        cx, cy = ex * (nx + 1) ** 2, ey * (ny + 1) ** 2
+        uu = u.view(ny, nx)
+        up = torch.nn.functional.pad(uu, (1, 1, 1, 1))
+        Au = (cx * (2 * uu - up[1:-1, :-2] - up[1:-1, 2:]) +
+              cy * (2 * uu - up[:-2, 1:-1] - up[2:, 1:-1]))
+        r = torch.linalg.norm(f.view(ny, nx) - Au).item()
+        assert r / torch.linalg.norm(f).item() < 1e-8, (p, st)
+        # the single-grid solve of the same problem
+        hs = S.srj_create(p["n"], eps=p["eps"], precision=S.SRJ_PREC_MIXED)
+        us = torch.zeros_like(f)
+        try:
+            s1 = S.srj_solve(hs, f.data_ptr(), us.data_ptr(), 1e-8)
+        finally:
+            S.srj_destroy(hs)
+        assert s1["status"] == S.SRJ_OK
+        lam = lam_min_const(p["n"], p["eps"])
+        bound = (r + s1["rn"]) / lam
+        assert torch.linalg.norm(u - us).item() <= bound * (1 + 1e-6) + 1e-12
