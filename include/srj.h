@@ -63,7 +63,11 @@ enum srj_selector {
     SRJ_SEL_HEURISTIC = 0,  /* Sec. 3, Alg. 1: ratio > 0.4 up, 0.2 < ratio < 0.4 down */
     SRJ_SEL_INCREASING = 1, /* Sec. 4: raise the level every cycle */
     SRJ_SEL_FIXED = 2,      /* stay at opts.fixed_level */
-    SRJ_SEL_MLP = 3,        /* learned selector (srj_mlp_set_weights), Alg. 1 as fallback */
+    SRJ_SEL_MLP = 3,        /* learned selector (srj_mlp_set_weights) with Alg. 1 as judge:
+                               after a picked cycle that did not shrink the residual, or
+                               shrank it more slowly per sweep (Sec. 3, Eq.
+                               average-convergence-rate) than the latest cycle Alg. 1
+                               chose, Alg. 1 takes the next decision */
     SRJ_SEL_JACOBI = 4      /* plain Jacobi, Sec. 2 Eq. (jacobi): omega = 1 every sweep, the
                                comparator of Sec. 4 and Table 3; the residual is tested
                                after every M(fixed_level) sweeps (a "cycle"; level 0:

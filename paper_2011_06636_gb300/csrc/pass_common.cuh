@@ -66,9 +66,17 @@ __device__ __forceinline__ int next_level(DevState *st, const SolveCfg &cfg, dou
                                           int level, int mlp_pick) {
     const int top = st->max_level;
     if (st->selector == DSEL_MLP) {
-        // the network picks; Alg. 1 judges: a picked cycle that did not shrink
-        // the residual hands the next decision back to Alg. 1
-        if (mlp_pick >= 0 && !(st->mlp_last && ratio >= 1.0)) {
+        // the network picks; Alg. 1 judges.  The finished cycle's average
+        // convergence rate (Sec. 3, Eq. average-convergence-rate; st->k is
+        // its M) is compared with that of the latest cycle Alg. 1 chose: a
+        // picked cycle that did not shrink the residual, or shrank it more
+        // slowly per sweep than Alg. 1's did, hands the next decision back to
+        // Alg. 1.  The first cycle counts as Alg. 1's.
+        const double rate = -log(ratio) / (double)(st->k > 0 ? st->k : 1);
+        bool take = mlp_pick >= 0;
+        if (st->mlp_last) take = take && ratio < 1.0 && rate >= st->alg1_rate;
+        else st->alg1_rate = rate;
+        if (take) {
             st->mlp_last = 1;
             return mlp_pick < top ? mlp_pick : top;
         }

@@ -95,6 +95,7 @@ struct DevState {
     int32_t nhist;
     int32_t mlp_last;       // 1 when the current cycle's level was the network's pick
     int32_t mlp_fallbacks;  // cycles whose level came from Alg. 1 after a failed pick
+    double alg1_rate;       // average convergence rate of the latest cycle Alg. 1 chose
     int32_t dim;
     double npoints;
     double dlast;  // SRJ_TOL_DINF: ||u^n - u^(n-1)||_inf of the latest sweep

@@ -85,11 +85,14 @@ def test_device_training_matches_oracle_adam(S):
 
 def _oracle_mlp_solve(orc, P, f, theta, tol, max_cycles=400):
     """The solver loop of Sec. 3 with the level chosen by the oracle network
-    among the moves {L-1, L, L+1} (ties to the lower level), Alg. 1 as
-    fallback after a picked cycle whose residual did not shrink."""
+    among the moves {L-1, L, L+1} (ties to the lower level) and Alg. 1 as
+    judge: after a picked cycle that did not shrink the residual, or shrank
+    it more slowly per sweep (average convergence rate, Sec. 3) than the
+    latest cycle Alg. 1 chose, Alg. 1 takes the next decision."""
     u = np.zeros(P.size)
     r0 = orc.residual_norm(P, u, f)
     rprev, level, hist, levels, by_mlp = r0, 0, [], [], False
+    alg1_rate = 0.0
     npts = P.size
     for _ in range(max_cycles):
         u, rn = orc.run_levels(P, f, u, [level])
@@ -97,10 +100,13 @@ def _oracle_mlp_solve(orc, P, f, theta, tol, max_cycles=400):
         levels.append(level)
         ratio = rn / rprev
         rprev = rn
+        rate = -math.log(ratio) / orc.level_m(level)
         hist = [min(5.0, max(-20.0, math.log(ratio)))] + hist
         if rn / r0 < tol:
             return u, levels
-        if by_mlp and ratio >= 1.0:
+        if not by_mlp:
+            alg1_rate = rate
+        if by_mlp and (ratio >= 1.0 or rate < alg1_rate):
             level = orc.next_level(0, ratio, level)
             by_mlp = False
         else:
