@@ -32,11 +32,12 @@ UNIT = "GLUP/s"
 SIDE = 4096
 TOL = 1e-8
 # FP32 instructions per grid-point update of the FP32-pair relaxation of the
-# isotropic 2D workload (df_t2d_iso + df_axpy in csrc/df32.cuh): five Knuth
-# two-sums (6 each), one exact scaling by 1/4, one FMA and eight plain
-# low-part adds for t (40); then one two-product, one FMA, one two-sum, two
-# adds and one Dekker renormalisation (3) for u + omega t (14).
-DF_OPS_PER_LUP = 46  # FP32 instructions per update of the isotropic FP32-pair form (32 + df_axpy 14)
+# isotropic 2D workload (df_pair_sum + df_relax_iso_pairs in csrc/df32.cuh):
+# the shared diagonal pair sum (8), the second pair sum (8), q = s/4 + g as an
+# error-free sum (6 + 1), the two products (1 - omega) u and omega q with
+# their errors (6), their error-free sum (6), two low-part adds and one Dekker
+# renormalisation (5).
+DF_OPS_PER_LUP = 40  # FP32 instructions per update of the fused isotropic FP32-pair form
 # algorithmic HBM bytes of an FP32 sweep per grid point and pass: read u, read
 # f, write u (4 B each); 3D variable coefficients add k (4 B)
 ALGO_BYTES_PER_POINT = 12.0

@@ -134,6 +134,100 @@ __device__ __forceinline__ df32 df_t_axes(const df32 *nb, const float *a, float 
     return df32{r.hi, __fsub_rn(__fadd_rn(sl, r.lo), u.lo)};
 }
 
+// One relaxed sweep at a point of the isotropic case, fused:
+//   u' = (1 - omega) u + omega q,   q = (p + q2) / 4 + g,
+// the same value as u + omega (q - u).  1 - omega is exact in FP32 for every
+// factor of the scheme tables (omega lies in (0.5, 2^24): for omega <= 2 by
+// Sterbenz's lemma, above 2 because 1 is a multiple of omega's last place).
+// Both products keep their rounding errors (two_prod) and meet in one
+// error-free sum, so no difference q - u is formed first: 40 FP32 operations
+// with the shared pair sum, against 46 for df_t2d_iso_pairs + df_axpy, in the
+// same accuracy class (every rounding left is of order eps^2 omega |u|).
+__device__ __forceinline__ df32 df_relax_iso_pairs(df32 p, df32 q2, float g, df32 u, float omega,
+                                                   float one_minus_omega) {
+    const df32 s = df_two_sum(p.hi, q2.hi);
+    const float slo = __fadd_rn(s.lo, __fadd_rn(p.lo, q2.lo));
+    // q = s / 4 + g: Knuth's two-sum of a = s / 4 (exact) and g with the
+    // quarter folded into FMAs (fl(a + g), fl(q - a) and fl(a - t) each round
+    // once, as the two-sum's own steps do): 6 operations for scale and sum
+    const float qh = __fmaf_rn(s.hi, 0.25f, g);
+    const float bb = __fmaf_rn(s.hi, -0.25f, qh);
+    const float t1 = __fsub_rn(qh, bb);
+    const float qe = __fadd_rn(__fmaf_rn(s.hi, 0.25f, -t1), __fsub_rn(g, bb));
+    const df32 qs{qh, qe};
+    const float qlo = __fmaf_rn(slo, 0.25f, qs.lo);
+    const df32 p1 = df_two_prod(one_minus_omega, u.hi);
+    const float e1 = __fmaf_rn(one_minus_omega, u.lo, p1.lo);
+    const df32 p2 = df_two_prod(omega, qs.hi);
+    const float e2 = __fmaf_rn(omega, qlo, p2.lo);
+    const df32 z = df_two_sum(p1.hi, p2.hi);
+    return df_fast_two_sum(z.hi, __fadd_rn(z.lo, __fadd_rn(e1, e2)));
+}
+
+// The value q a sweep relaxes towards, u' = u + omega (q - u), as an
+// unnormalised FP32 pair (its low part carries every rounding error):
+//   variable coefficients   q = invd (f + sum_q w_q n_q)        11 NQ + 3 ops
+//   constant, NA axes       q = sum_a a_a (n_2a + n_2a+1) + g   19 NA ops
+//   2D constant (general)   q = ax (w + e) + ay (s + n) + g     38 ops
+template <int NQ>
+__device__ __forceinline__ df32 df_q_vark(const df32 *nb, const float *w, float invd, float f) {
+    float sh = f, sl = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const df32 pq = df_two_prod(nb[q].hi, w[q]);
+        const float pl = __fmaf_rn(nb[q].lo, w[q], pq.lo);
+        const df32 sq = df_two_sum(sh, pq.hi);
+        sh = sq.hi;
+        sl = __fadd_rn(sl, __fadd_rn(sq.lo, pl));
+    }
+    const df32 m = df_two_prod(sh, invd);
+    return df32{m.hi, __fmaf_rn(sl, invd, m.lo)};
+}
+
+template <int NA>
+__device__ __forceinline__ df32 df_q_axes(const df32 *nb, const float *a, float g) {
+    float sh = g, sl = 0.f;
+#pragma unroll
+    for (int ax = 0; ax < NA; ++ax) {
+        const df32 s = df_two_sum(nb[2 * ax].hi, nb[2 * ax + 1].hi);
+        const float slo = __fadd_rn(s.lo, __fadd_rn(nb[2 * ax].lo, nb[2 * ax + 1].lo));
+        const df32 p = df_two_prod(s.hi, a[ax]);
+        const float pl = __fmaf_rn(slo, a[ax], p.lo);
+        const df32 q = df_two_sum(sh, p.hi);
+        sh = q.hi;
+        sl = __fadd_rn(sl, __fadd_rn(q.lo, pl));
+    }
+    return df32{sh, sl};
+}
+
+__device__ __forceinline__ df32 df_q_2d(df32 w, df32 e, df32 s, df32 n, float ax, float ay,
+                                        float g) {
+    const df32 sx = df_two_sum(w.hi, e.hi);
+    const float sxl = __fadd_rn(sx.lo, __fadd_rn(w.lo, e.lo));
+    const df32 sy = df_two_sum(s.hi, n.hi);
+    const float syl = __fadd_rn(sy.lo, __fadd_rn(s.lo, n.lo));
+    const df32 px = df_two_prod(sx.hi, ax);
+    const float pxl = __fmaf_rn(sxl, ax, px.lo);
+    const df32 py = df_two_prod(sy.hi, ay);
+    const float pyl = __fmaf_rn(syl, ay, py.lo);
+    const df32 q = df_two_sum(px.hi, py.hi);
+    const df32 r1 = df_two_sum(q.hi, g);
+    return df32{r1.hi, __fadd_rn(__fadd_rn(q.lo, __fadd_rn(pxl, pyl)), r1.lo)};
+}
+
+// u' = (1 - omega) u + omega q with both products' rounding errors kept and
+// one renormalisation: the same value as u + omega (q - u) without forming
+// the difference (1 - omega is exact in FP32 for the scheme's factors; see
+// df_relax_iso_pairs).  17 FP32 operations.
+__device__ __forceinline__ df32 df_relax_to(df32 u, df32 q, float omega, float one_minus_omega) {
+    const df32 p1 = df_two_prod(one_minus_omega, u.hi);
+    const float e1 = __fmaf_rn(one_minus_omega, u.lo, p1.lo);
+    const df32 p2 = df_two_prod(omega, q.hi);
+    const float e2 = __fmaf_rn(omega, q.lo, p2.lo);
+    const df32 z = df_two_sum(p1.hi, p2.hi);
+    return df_fast_two_sum(z.hi, __fadd_rn(z.lo, __fadd_rn(e1, e2)));
+}
+
 // u + omega t with one renormalisation (about 14 FP32 operations).
 __device__ __forceinline__ df32 df_axpy(df32 u, df32 t, float omega) {
     const df32 d = df_two_prod(t.hi, omega);

@@ -119,17 +119,23 @@ __global__ void __launch_bounds__(kBlock) generic_pass_kernel(PassLaunch a, int 
                     wgt[4] = z > 0 ? __ldg(wz + i - g.plane) : C(0);
                     wgt[5] = __ldg(wz + i);
                 }
-                t = P::t_of(nb, wgt, invd_i, fi, u_c);
-                diag_i = C(1) / invd_i;
-            } else {
-                t = P::t_const(nb, cconst, invd_c, fi, u_c);
-            }
-            if (p.nsw) {
-                const T un = P::relax(u_c, t, omega);
+                if (p.nsw) {
+                    const T un = P::sweep_of(nb, wgt, invd_i, fi, u_c, omega);
+                    store_u<PREC>(a.bufs, dst, i, un);
+                    if constexpr (PREC != PREC_DF)
+                        if (dinf) dbits = max_bits(dbits, abs_diff_bits((double)un, (double)u_c));
+                } else {
+                    t = P::t_of(nb, wgt, invd_i, fi, u_c);
+                    diag_i = C(1) / invd_i;
+                    part += P::resid2(t, diag_i);
+                }
+            } else if (p.nsw) {
+                const T un = P::sweep_const(nb, cconst, invd_c, fi, u_c, omega);
                 store_u<PREC>(a.bufs, dst, i, un);
                 if constexpr (PREC != PREC_DF)
                     if (dinf) dbits = max_bits(dbits, abs_diff_bits((double)un, (double)u_c));
             } else {
+                t = P::t_const(nb, cconst, invd_c, fi, u_c);
                 part += P::resid2(t, diag_i);
             }
             u_zm = u_c;

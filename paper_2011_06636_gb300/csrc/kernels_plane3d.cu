@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kTX * kTY)
             nb[4] = u_m;
             nb[5] = ldu(sp, tx, ty);
             const C fi = ld(s0, L::o_f, tid);
-            T t;
+            T t = zero_u<PREC>(), un = zero_u<PREC>();
             C invd_i = invd_c;
             if constexpr (VARK) {
                 C wgt[6];
@@ -231,13 +231,14 @@ __global__ void __launch_bounds__(kTX * kTY)
                 wgt[5] = ld(s0, L::o_wz, tid);
                 wz_m = wgt[5];
                 invd_i = ld(s0, L::o_id, tid);
-                t = P::t_of(nb, wgt, invd_i, fi, u_c);
+                if (p.nsw) un = P::sweep_of(nb, wgt, invd_i, fi, u_c, omega);
+                else t = P::t_of(nb, wgt, invd_i, fi, u_c);
             } else {
-                t = P::t_const(nb, cconst, invd_c, fi, u_c);
+                if (p.nsw) un = P::sweep_const(nb, cconst, invd_c, fi, u_c, omega);
+                else t = P::t_const(nb, cconst, invd_c, fi, u_c);
             }
             const long long i = col + (long long)g.plane * z;
             if (p.nsw) {
-                const T un = P::relax(u_c, t, omega);
                 store_u<PREC>(a.bufs, dst, i, un);
                 if constexpr (PREC != PREC_DF)
                     if (dinf) dbits = max_bits(dbits, abs_diff_bits((double)un, (double)u_c));
@@ -491,7 +492,6 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
                 nb[4] = um1[k];
                 nb[5] = up;
                 const C fi = ldc(s0, L::o_f, i);
-                T t;
                 if constexpr (VARK) {
                     C wgt[6];
                     wgt[0] = ldc(s0, L::o_wx, i - 1);
@@ -500,11 +500,10 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
                     wgt[3] = ldc(s0, L::o_wy, i);
                     wgt[4] = wzm1[k];
                     wgt[5] = wzp;
-                    t = P::t_of(nb, wgt, ldc(s0, L::o_id, i), fi, uc1[k]);
+                    val = P::sweep_of(nb, wgt, ldc(s0, L::o_id, i), fi, uc1[k], om1);
                 } else {
-                    t = P::t_const(nb, cconst, invd_c, fi, uc1[k]);
+                    val = P::sweep_const(nb, cconst, invd_c, fi, uc1[k], om1);
                 }
-                val = P::relax(uc1[k], t, om1);
             }
             l1z[tid + kT2Threads * k] = val;
             um1[k] = uc1[k];
@@ -526,15 +525,14 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
                 nb[3] = l1m[li2[q] + kL1W];
                 nb[4] = vm2[q];
                 nb[5] = vp;
-                T t;
+                T un;
                 if constexpr (VARK) {
                     C wgt[6] = {cwxm[q], cwxp[q], cwym[q], cwyp[q], cwzm[q], cwzp[q]};
-                    t = P::t_of(nb, wgt, cid[q], cf[q], vc2[q]);
+                    un = P::sweep_of(nb, wgt, cid[q], cf[q], vc2[q], om2);
                 } else {
-                    t = P::t_const(nb, cconst, invd_c, cf[q], vc2[q]);
+                    un = P::sweep_const(nb, cconst, invd_c, cf[q], vc2[q], om2);
                 }
-                store_u<PREC>(a.bufs, dst, col2[q] + (long long)g.plane * (z - 1),
-                              P::relax(vc2[q], t, om2));
+                store_u<PREC>(a.bufs, dst, col2[q] + (long long)g.plane * (z - 1), un);
             }
             vm2[q] = vc2[q];
             vc2[q] = vp;

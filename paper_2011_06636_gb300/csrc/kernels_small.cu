@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(PassLaunch a
                 nb[5] = z + 1 < nz ? ld(i + pl) : (nz_ ? ld(i - pl) : zero);
             }
             const T uc = ld(i);
-            T t;
+            T t = zero_u<PREC>(), un_v = zero_u<PREC>();
             C diag_i = diag_c;
             if constexpr (VARK) {
                 C w[6];
@@ -134,13 +134,19 @@ __global__ void __launch_bounds__(kSmallThreads) small_solve_kernel(PassLaunch a
                     w[4] = z > 0 ? swz[i - nx * ny] : C(0);
                     w[5] = swz[i];
                 }
-                t = P::t_of(nb, w, sid[i], sf[i], uc);
-                diag_i = C(1) / sid[i];
+                if (p.nsw) {
+                    un_v = P::sweep_of(nb, w, sid[i], sf[i], uc, omega);
+                } else {
+                    t = P::t_of(nb, w, sid[i], sf[i], uc);
+                    diag_i = C(1) / sid[i];
+                }
+            } else if (p.nsw) {
+                un_v = P::sweep_const(nb, cconst, invd_c, sf[i], uc, omega);
             } else {
                 t = P::t_const(nb, cconst, invd_c, sf[i], uc);
             }
             if (p.nsw) {
-                const T un = P::relax(uc, t, omega);
+                const T un = un_v;
                 if constexpr (LO) {
                     s_hi[dst][i] = un.hi;
                     s_lo[dst][i] = un.lo;

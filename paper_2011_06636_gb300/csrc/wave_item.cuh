@@ -29,6 +29,12 @@
 #include "stencil_point.cuh"
 #include "srj_internal.h"
 
+// The FP32-pair isotropic levels use the fused relaxation df_relax_iso_pairs
+// (define SRJ_DF_RELAX_FUSED=0 for the two-step form).
+#ifndef SRJ_DF_RELAX_FUSED
+#define SRJ_DF_RELAX_FUSED 1
+#endif
+
 namespace srj {
 namespace {
 
@@ -123,6 +129,7 @@ struct ItemCtx {
     E *dst;
     float *dst_hi, *dst_lo;
     C omega[T];
+    C omega1m[T];  // 1 - omega, exact in FP32 for the scheme's factors
     int nsw;     // sweeps of this pass (levels beyond nsw are identities)
     int resid;   // 1: accumulate the residual of the final state
     int iso;     // FP32 pair or FP64 with acoef = {1/4, 1/4}: the isotropic stencil form
@@ -324,8 +331,15 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const E uc = ring[s - 1][S2][v];
-                    const E tt = Point<PREC, 2>::t_iso_pairs(
-                        pc[v], v > 0 ? pprev[s - 1][v - 1] : pleft, c.invd, fv[v], uc);
+                    const E pl = v > 0 ? pprev[s - 1][v - 1] : pleft;
+#if SRJ_DF_RELAX_FUSED
+                    if constexpr (LO) {
+                        ring[s][S3][v] = df_relax_iso_pairs(pc[v], pl, fv[v], uc, c.omega[s - 1],
+                                                            c.omega1m[s - 1]);
+                        continue;
+                    }
+#endif
+                    const E tt = Point<PREC, 2>::t_iso_pairs(pc[v], pl, c.invd, fv[v], uc);
                     ring[s][S3][v] = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
                 }
 #pragma unroll
@@ -341,8 +355,8 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
                     nb[2] = ring[s - 1][S3][v];
                     nb[3] = ring[s - 1][S1][v];
                     const E uc = ring[s - 1][S2][v];
-                    const E tt = Point<PREC, 2>::t_const(nb, c.acoef, c.invd, fv[v], uc);
-                    ring[s][S3][v] = Point<PREC, 2>::relax(uc, tt, (double)c.omega[s - 1]);
+                    ring[s][S3][v] = Point<PREC, 2>::sweep_const(nb, c.acoef, c.invd, fv[v], uc,
+                                                                 (double)c.omega[s - 1]);
                 }
             }
             // Dirichlet ghosts stay zero (a warp-uniform test: the row is the
@@ -471,7 +485,10 @@ __device__ __forceinline__ void fill_ctx(ItemCtx<PREC, T> &c, const GridGeo &g,
     c.dst_hi = (float *)b.u[cur ^ 1];
     c.dst_lo = (float *)b.ulo[cur ^ 1];
 #pragma unroll
-    for (int s = 0; s < T; ++s) c.omega[s] = (s < nsw) ? (C)w64[woff + s] : C(0);
+    for (int s = 0; s < T; ++s) {
+        c.omega[s] = (s < nsw) ? (C)w64[woff + s] : C(0);
+        c.omega1m[s] = C(1) - c.omega[s];
+    }
     c.nsw = nsw;
     c.resid = resid;
     c.diag = C(g.diag);

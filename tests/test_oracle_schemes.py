@@ -158,3 +158,16 @@ def test_cycle_is_order_independent_and_growth_bounded(orc, level):
         for wi in wr:
             Q *= (1 - wi) + wi * lam
         assert np.max(np.abs(P - Q)) < 1e-9
+
+
+def test_one_minus_omega_is_exact_in_fp32(orc):
+    """The fused FP32-pair relaxation forms (1 - omega) u + omega q with
+    1 - omega computed in FP32: exact for every factor of the 25 levels,
+    because each lies in (0.5, 2^24) (Sterbenz's lemma up to 2, a multiple of
+    omega's last place above)."""
+    import numpy as np
+    for level in range(25):
+        w32 = orc.level_omegas(level).astype(np.float32)
+        assert np.all(w32 > 0.5) and np.all(w32 < 2.0 ** 24)
+        one_minus = np.float32(1.0) - w32
+        assert np.array_equal(one_minus.astype(np.float64), 1.0 - w32.astype(np.float64))
