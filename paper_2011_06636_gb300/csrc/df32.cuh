@@ -143,6 +143,7 @@ __device__ __forceinline__ df32 df_t_axes(const df32 *nb, const float *a, float 
 // error-free sum, so no difference q - u is formed first: 40 FP32 operations
 // with the shared pair sum, against 46 for df_t2d_iso_pairs + df_axpy, in the
 // same accuracy class (every rounding left is of order eps^2 omega |u|).
+template <bool RENORM = true>
 __device__ __forceinline__ df32 df_relax_iso_pairs(df32 p, df32 q2, float g, df32 u, float omega,
                                                    float one_minus_omega) {
     const df32 s = df_two_sum(p.hi, q2.hi);
@@ -161,7 +162,14 @@ __device__ __forceinline__ df32 df_relax_iso_pairs(df32 p, df32 q2, float g, df3
     const df32 p2 = df_two_prod(omega, qs.hi);
     const float e2 = __fmaf_rn(omega, qlo, p2.lo);
     const df32 z = df_two_sum(p1.hi, p2.hi);
-    return df_fast_two_sum(z.hi, __fadd_rn(z.lo, __fadd_rn(e1, e2)));
+    const float lo = __fadd_rn(z.lo, __fadd_rn(e1, e2));
+    // without the renormalisation the pair stays an unevaluated sum whose low
+    // part may exceed half an ulp of the high part; every later use takes the
+    // high parts through error-free sums and adds the low parts plainly, so
+    // the roundings stay of the same order (used for the levels of a pass
+    // that are not stored)
+    if constexpr (!RENORM) return df32{z.hi, lo};
+    return df_fast_two_sum(z.hi, lo);
 }
 
 // The value q a sweep relaxes towards, u' = u + omega (q - u), as an

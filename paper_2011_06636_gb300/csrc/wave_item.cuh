@@ -34,6 +34,9 @@
 #ifndef SRJ_DF_RELAX_FUSED
 #define SRJ_DF_RELAX_FUSED 1
 #endif
+#ifndef SRJ_DF_SKIP_RENORM
+#define SRJ_DF_SKIP_RENORM 1
+#endif
 
 namespace srj {
 namespace {
@@ -334,8 +337,13 @@ __device__ __forceinline__ double wave_item_impl(const ItemCtx<PREC, T> &c, int 
                     const E pl = v > 0 ? pprev[s - 1][v - 1] : pleft;
 #if SRJ_DF_RELAX_FUSED
                     if constexpr (LO) {
-                        ring[s][S3][v] = df_relax_iso_pairs(pc[v], pl, fv[v], uc, c.omega[s - 1],
-                                                            c.omega1m[s - 1]);
+                        // only the level that is stored renormalises its pair
+                        if (SRJ_DF_SKIP_RENORM && s < T)
+                            ring[s][S3][v] = df_relax_iso_pairs<false>(
+                                pc[v], pl, fv[v], uc, c.omega[s - 1], c.omega1m[s - 1]);
+                        else
+                            ring[s][S3][v] = df_relax_iso_pairs<true>(
+                                pc[v], pl, fv[v], uc, c.omega[s - 1], c.omega1m[s - 1]);
                         continue;
                     }
 #endif
