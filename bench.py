@@ -65,8 +65,8 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "wave2d_fp32pair_T2_4096.md")
 # the same for the 3D mixed solve's pass (captured at 256^3: its traffic is
 # scaled to the bench's grid by the points of a launch)
 KERNEL_SOURCES_3D = ["paper_2011_06636_gb300/csrc/" + f for f in (
-    "kernels_plane3d.cu", "df32.cuh", "stencil_point.cuh", "pass_common.cuh", "mlp.cuh",
-    "srj_internal.h")]
+    "kernels_plane3d.cu", "df32.cuh", "df32x2.cuh", "stencil_point.cuh", "pass_common.cuh",
+    "mlp.cuh", "srj_internal.h")]
 PROFILE_SUMMARY_3D = os.path.join(ROOT, "profiles", "plane3d2_fp32pair_vark_256.md")
 PROFILE_POINTS_3D = 256 ** 3
 

@@ -15,8 +15,10 @@
 #include <stdint.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "df32.cuh"
+#include "df32x2.cuh"
 #include "pass_common.cuh"
 #include "stencil_point.cuh"
 #include "srj_internal.h"
@@ -273,21 +275,26 @@ __global__ void __launch_bounds__(kTX * kTY)
 // 1/D) arrive by TMA in one box shape {40, 20} from (x0 - 4, y0 - 2): four
 // ring slots, planes issued up to three ahead.  At step z, level 1 (the first
 // sweep of the pass) computes plane z on the tile plus a one-cell halo (34 x
-// 18 points, a fixed set of two or three per thread) into a two-plane ring of
-// level-1 values; after a block barrier, level 2 (the second sweep) computes
-// plane z - 1 of the tile (two points per thread) from the level-1 ring and
-// stores it.  Each thread carries the z neighbours of its points and the
-// -z face weights in registers from plane to plane, and level 2 reads the
-// coefficients of its next plane one step ahead, so no slot is needed after
-// the step that last reads it.  Level-1 values outside the grid are zero (the
-// Dirichlet ghosts).  Only passes of two sweeps run here; the last pass of a
-// cycle (fewer sweeps, the residual) runs in plane3d_kernel.
+// 18 points) into a two-plane ring of level-1 values; after a block barrier,
+// level 2 (the second sweep) computes plane z - 1 of the tile from the
+// level-1 ring and stores it.  Thread (tx, ty) owns the tile points (tx, ty)
+// and (tx, ty + 8) at both levels; the 100 points of the halo ring belong to
+// threads 0 .. 99.  A thread's two points therefore pass from level 1 to
+// level 2 in registers: the level-1 value (level 2's +z neighbour) and every
+// coefficient level 1 read for the plane (level 2 uses them one step later);
+// only the four in-plane neighbours come from the level-1 ring.  The z
+// neighbours and the -z face weights are carried from plane to plane.  In
+// the FP32-pair form the two points of a thread are the two components of
+// packed FP32 instructions (df2).  Level-1 values outside the grid are zero
+// (the Dirichlet ghosts).  Only passes of two sweeps run here; the last pass
+// of a cycle (fewer sweeps, the residual) runs in plane3d_kernel.
 constexpr int kT2Y = 16;              // output rows per tile (two per thread)
 constexpr int kBW = 40, kBH = 20;     // staged box: columns x0-4 .., rows y0-2 ..
 constexpr int kL1W = 34, kL1H = 18;   // level-1 region: columns x0-1 .., rows y0-1 ..
 constexpr int kL1N = kL1W * kL1H;     // 612 points
 constexpr int kNS2 = 4;               // input ring slots
 constexpr int kT2Threads = kTX * kTY;  // 256
+constexpr int kL1Lo = al128(kL1N * 4);  // FP32 pair: offset of a level-1 plane's low part
 
 template <int PREC, bool VARK>
 struct Plane2 {
@@ -300,9 +307,71 @@ struct Plane2 {
     static constexpr int o_wz = o_wy + (VARK ? BOX : 0), o_id = o_wz + (VARK ? BOX : 0);
     static constexpr int BYTES = o_id + (VARK ? BOX : 0);    // one ring slot
     static constexpr unsigned TX = (unsigned)BYTES;          // bytes a plane's copies deliver
-    static constexpr int L1B = al128(kL1N * (int)sizeof(T));  // one level-1 plane
+    // one level-1 plane (the FP32 pair as separate high and low planes)
+    static constexpr int L1B = LO ? 2 * kL1Lo : al128(kL1N * (int)sizeof(T));
     static constexpr int SMEM = kNS2 * BYTES + 2 * L1B;
     static constexpr int MINB = SMEM > 113 * 1024 ? 1 : 2;   // CTAs per SM the smem allows
+};
+
+// The two tile points of a thread at one level, side by side.  FP32 pair:
+// the components of df2 (packed FP32 instructions); FP32 and FP64: a pair of
+// scalar points.  Staged arrays are read at slot offsets, level-1 planes at
+// level-1 indices (the FP32 pair as a high plane followed by a low plane).
+template <int PREC, bool VARK>
+struct Two3 {
+    using T = typename Elem<PREC>::T;
+    using C = typename Elem<PREC>::C;
+    using L = Plane2<PREC, VARK>;
+    using P = Point<PREC, 3>;
+    struct V {
+        T p[2];
+    };
+    struct W {
+        C p[2];
+    };
+
+    __device__ __forceinline__ static T ld1(const unsigned char *pl, int i) {
+        if constexpr (PREC == PREC_DF)
+            return df32{((const float *)pl)[i], ((const float *)(pl + kL1Lo))[i]};
+        else
+            return ((const T *)pl)[i];
+    }
+    __device__ __forceinline__ static void st1(unsigned char *pl, int i, T v) {
+        if constexpr (PREC == PREC_DF) {
+            ((float *)pl)[i] = v.hi;
+            ((float *)(pl + kL1Lo))[i] = v.lo;
+        } else {
+            ((T *)pl)[i] = v;
+        }
+    }
+    __device__ __forceinline__ static T ldu(const unsigned char *s, int i) {
+        if constexpr (PREC == PREC_DF)
+            return df32{*(const float *)(s + L::o_hi + i * 4), *(const float *)(s + L::o_lo + i * 4)};
+        else
+            return *(const T *)(s + L::o_hi + i * L::ES);
+    }
+    __device__ __forceinline__ static C ldc(const unsigned char *s, int off, int i) {
+        return *(const C *)(s + off + i * L::ES);
+    }
+};
+
+template <bool VARK>
+struct Two3DF {
+    using L = Plane2<PREC_DF, VARK>;
+    using V = df2;
+    using W = float2;
+    __device__ __forceinline__ static df2 ldu(const unsigned char *s, int i0, int i1) {
+        const float *h = (const float *)(s + L::o_hi), *l = (const float *)(s + L::o_lo);
+        return df2{make_float2(h[i0], h[i1]), make_float2(l[i0], l[i1])};
+    }
+    __device__ __forceinline__ static float2 ldc(const unsigned char *s, int off, int i0, int i1) {
+        const float *c = (const float *)(s + off);
+        return make_float2(c[i0], c[i1]);
+    }
+    __device__ __forceinline__ static df2 ld1(const unsigned char *pl, int i0, int i1) {
+        const float *h = (const float *)pl, *l = (const float *)(pl + kL1Lo);
+        return df2{make_float2(h[i0], h[i1]), make_float2(l[i0], l[i1])};
+    }
 };
 
 template <int PREC, bool VARK>
@@ -312,6 +381,12 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
     using C = typename Elem<PREC>::C;
     using P = Point<PREC, 3>;
     using L = Plane2<PREC, VARK>;
+    using S = Two3<PREC, VARK>;
+    constexpr bool DF = PREC == PREC_DF;
+    using D = Two3DF<VARK>;
+    // a thread's two points: packed pairs (FP32 pair) or two scalars
+    using V = std::conditional_t<DF, df2, typename S::V>;
+    using W = std::conditional_t<DF, float2, typename S::W>;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_bar[kNS2];
     __shared__ PassPlan s_plan;
@@ -341,6 +416,7 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
     if (!s_mine) return;
     const PassPlan p = s_plan;
     const double om1 = s_om[0], om2 = s_om[1];
+    const float om1f = (float)om1, om2f = (float)om2;
     const long long wlim = s_wlim;
 
     const GridGeo &g = a.geo;
@@ -373,18 +449,11 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
     auto wait = [&](int zz, long long limit) -> bool {
         return bar_wait(&s_bar[rel(zz) % kNS2], (unsigned)((rel(zz) / kNS2) & 1), limit);
     };
-    // staged arrays: index of column lx (-4 .. 35), row ly (-2 .. 17) of the tile
+    // staged arrays: index of column lx (-4 .. 35), row ly (-2 .. 17) of the tile;
+    // level-1 planes: column lx (-1 .. 32), row ly (-1 .. 16)
     auto sidx = [](int lx, int ly) { return (lx + kHX) + kBW * (ly + 2); };
-    auto ldc = [&](const unsigned char *s, int off, int i) -> C {
-        return *(const C *)(s + off + i * L::ES);
-    };
-    auto ldu = [&](const unsigned char *s, int i) -> T {
-        if constexpr (L::LO)
-            return df32{*(const float *)(s + L::o_hi + i * 4), *(const float *)(s + L::o_lo + i * 4)};
-        else
-            return *(const T *)(s + L::o_hi + i * L::ES);
-    };
-    auto l1 = [&](int zz) -> T * { return (T *)(l1b + (zz & 1) * L::L1B); };
+    auto lidx = [](int lx, int ly) { return (lx + 1) + kL1W * (ly + 1); };
+    auto l1 = [&](int zz) -> unsigned char * { return l1b + (zz & 1) * L::L1B; };
 
     C cconst[3];
     const C invd_c = C(g.invdiag);
@@ -392,30 +461,36 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
     cconst[1] = C(g.acy);
     cconst[2] = C(g.acz);
 
-    // level-1 points of this thread: q = tid + 256 k, column q % 34 - 1,
-    // row q / 34 - 1 of the tile; and level-2 points: column tx, rows ty, ty + 8
-    constexpr int K1 = (kL1N + kT2Threads - 1) / kT2Threads;  // 3
-    int si1[K1];
-    bool has1[K1], in1[K1];
-#pragma unroll
-    for (int k = 0; k < K1; ++k) {
-        const int q = tid + kT2Threads * k;
-        has1[k] = q < kL1N;
-        const int lx = q % kL1W - 1, ly = q / kL1W - 1;
-        si1[k] = sidx(lx, ly);
-        const int gx = x0 + lx, gy = y0 + ly;
-        in1[k] = has1[k] && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
-    }
-    int si2[2], li2[2];
-    bool in2[2];
-    long long col2[2];
+    // the thread's tile points (tx, ty + 8 q), q = 0, 1
+    int si[2], li[2];
+    bool in[2];
+    long long col[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int ly = ty + 8 * q;
-        si2[q] = sidx(tx, ly);
-        li2[q] = (tx + 1) + kL1W * (ly + 1);
-        in2[q] = (x0 + tx) < g.nx && (y0 + ly) < g.ny;
-        col2[q] = (long long)(x0 + tx) + g.pitch * (y0 + ly);
+        si[q] = sidx(tx, ly);
+        li[q] = lidx(tx, ly);
+        in[q] = (x0 + tx) < g.nx && (y0 + ly) < g.ny;
+        col[q] = (long long)(x0 + tx) + g.pitch * (y0 + ly);
+    }
+    // the halo ring (100 points: rows -1 and 16 over columns -1 .. 32, then
+    // columns -1 and 32 over rows 0 .. 15): threads 0 .. 49 own ring points
+    // tid and tid + 50, side by side like the tile points
+    constexpr int kRing = 2 * kL1W + 2 * kT2Y;
+    const bool hasH = tid < kRing / 2;
+    int siH[2], liH[2];
+    bool inH[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int h = tid + q * (kRing / 2);
+        int hx, hy;
+        if (h < kL1W) hx = h - 1, hy = -1;
+        else if (h < 2 * kL1W) hx = h - kL1W - 1, hy = kT2Y;
+        else if (h < 2 * kL1W + kT2Y) hx = -1, hy = h - 2 * kL1W;
+        else hx = kTX, hy = h - 2 * kL1W - kT2Y;
+        siH[q] = sidx(hx, hy);
+        liH[q] = lidx(hx, hy);
+        inH[q] = hasH && x0 + hx >= 0 && x0 + hx < g.nx && y0 + hy >= 0 && y0 + hy < g.ny;
     }
 
     if (tid == 0)
@@ -424,26 +499,81 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
     int next_wait = z0 - 2;  // first plane this thread has not seen land
     bool ok = true;
 
-    // carried values: level 1 -- the iterate at z - 1 and z and the -z face;
-    // level 2 -- level-1 values at z - 2 and z - 1 and the coefficients of the
-    // plane it computes next
-    T um1[K1], uc1[K1];
-    C wzm1[K1];
+    // loads of two points (the tile pair or the ring pair) side by side
+    auto ld_u2 = [&](const unsigned char *s, const int *ix, int d) -> V {
+        if constexpr (DF) return D::ldu(s, ix[0] + d, ix[1] + d);
+        else return V{{S::ldu(s, ix[0] + d), S::ldu(s, ix[1] + d)}};
+    };
+    auto ld_c2 = [&](const unsigned char *s, int off, const int *ix, int d) -> W {
+        if constexpr (DF) return D::ldc(s, off, ix[0] + d, ix[1] + d);
+        else return W{{S::ldc(s, off, ix[0] + d), S::ldc(s, off, ix[1] + d)}};
+    };
+    auto ld_l1 = [&](const unsigned char *pl, int d) -> V {
+        if constexpr (DF) return D::ld1(pl, li[0] + d, li[1] + d);
+        else return V{{S::ld1(pl, li[0] + d), S::ld1(pl, li[1] + d)}};
+    };
+    auto zero2 = [&]() -> V {
+        if constexpr (DF) return df2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        else return V{{zero_u<PREC>(), zero_u<PREC>()}};
+    };
+    auto wzero2 = [&]() -> W {
+        if constexpr (DF) return make_float2(0.f, 0.f);
+        else return W{{C(0), C(0)}};
+    };
+    auto get = [&](const V &v, int q) -> T {
+        if constexpr (DF) return q ? df32{v.hi.y, v.lo.y} : df32{v.hi.x, v.lo.x};
+        else return v.p[q];
+    };
+    // point q keeps its value where k[q], else zero (ghost)
+    auto keep = [&](V v, bool k0, bool k1) -> V {
+        if constexpr (DF) {
+            if (!k0) v.hi.x = v.lo.x = 0.f;
+            if (!k1) v.hi.y = v.lo.y = 0.f;
+            return v;
+        } else {
+            if (!k0) v.p[0] = zero_u<PREC>();
+            if (!k1) v.p[1] = zero_u<PREC>();
+            return v;
+        }
+    };
+    // one relaxed sweep of the two points
+    auto sweep2 = [&](const V *nb, const W *wgt, W invd, W f, const V &uc, double om,
+                      float omf) -> V {
+        if constexpr (DF) {
+            df2 q;
+            if constexpr (VARK) q = df2_q_vark<6>(nb, wgt, invd, f);
+            else q = df2_q_axes<3>(nb, cconst, f);
+            return df2_relax_to(uc, q, omf, 1.f - omf);
+        } else {
+            V r;
 #pragma unroll
-    for (int k = 0; k < K1; ++k) {
-        um1[k] = zero_u<PREC>();
-        uc1[k] = zero_u<PREC>();
-        wzm1[k] = C(0);
-    }
-    T vm2[2], vc2[2];
-    C cf[2], cwxm[2], cwxp[2], cwym[2], cwyp[2], cwzm[2], cwzp[2], cid[2];
+            for (int k = 0; k < 2; ++k) {
+                T n1[6];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        vm2[q] = zero_u<PREC>();
-        vc2[q] = zero_u<PREC>();
-        cf[q] = cwxm[q] = cwxp[q] = cwym[q] = cwyp[q] = cwzm[q] = cwzp[q] = C(0);
-        cid[q] = invd_c;
-    }
+                for (int j = 0; j < 6; ++j) n1[j] = nb[j].p[k];
+                if constexpr (VARK) {
+                    C w1[6];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) w1[j] = wgt[j].p[k];
+                    r.p[k] = P::sweep_of(n1, w1, invd.p[k], f.p[k], uc.p[k], om);
+                } else {
+                    r.p[k] = P::sweep_const(n1, cconst, invd_c, f.p[k], uc.p[k], om);
+                }
+            }
+            return r;
+        }
+    };
+
+    // carried values.  Level 1: the iterate at z - 1 and z, the -z face.
+    // Level 2: level-1 values at z - 2 and z - 1, and the coefficients level 1
+    // read for plane z - 1 (f, faces -x +x -y +y -z +z, 1/D).
+    V um1 = zero2(), uc1 = zero2(), vm2 = zero2(), vc2 = zero2();
+    W wzm1 = wzero2();
+    W cw[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) cw[j] = wzero2();
+    V um1H = zero2(), uc1H = zero2();
+    W wzm1H = wzero2();
 
     for (int z = z0 - 1; z <= z1; ++z) {
         // planes z and z + 1 (and, at the first step, z - 1) must have landed
@@ -467,87 +597,73 @@ __global__ void __launch_bounds__(kT2Threads, (Plane2<PREC, VARK>::MINB))
         }
         const unsigned char *s0 = slot(z), *sp = slot(z + 1);
         const bool zin = z >= 0 && z < g.nz;
-        T *l1z = l1(z);
-        // level 1: plane z of the tile plus halo
-#pragma unroll
-        for (int k = 0; k < K1; ++k) {
-            if (!has1[k]) continue;
-            const int i = si1[k];
+        unsigned char *l1z = l1(z);
+        // level 1 on a pair of points of plane z (ix: staged indices, jx:
+        // level-1 indices, k: inside the grid); um, uc, wzm: the carried
+        // iterate at z - 1 and z and -z face; nc returns the coefficients read
+        auto level1 = [&](const int *ix, const int *jx, const bool *k, V &um, V &uc, W &wzm,
+                          W *nc) -> V {
             if (z == z0 - 1) {  // the first step reads what later steps carry
                 const unsigned char *sm = slot(z - 1);
-                um1[k] = ldu(sm, i);
-                uc1[k] = ldu(s0, i);
-                if constexpr (VARK) wzm1[k] = ldc(sm, L::o_wz, i);
+                um = ld_u2(sm, ix, 0);
+                uc = ld_u2(s0, ix, 0);
+                if constexpr (VARK) wzm = ld_c2(sm, L::o_wz, ix, 0);
             }
-            const T up = ldu(sp, i);
-            T val = zero_u<PREC>();
-            C wzp = C(0);
-            if constexpr (VARK) wzp = ldc(s0, L::o_wz, i);
-            if (in1[k] && zin) {
-                T nb[6];
-                nb[0] = ldu(s0, i - 1);
-                nb[1] = ldu(s0, i + 1);
-                nb[2] = ldu(s0, i - kBW);
-                nb[3] = ldu(s0, i + kBW);
-                nb[4] = um1[k];
-                nb[5] = up;
-                const C fi = ldc(s0, L::o_f, i);
-                if constexpr (VARK) {
-                    C wgt[6];
-                    wgt[0] = ldc(s0, L::o_wx, i - 1);
-                    wgt[1] = ldc(s0, L::o_wx, i);
-                    wgt[2] = ldc(s0, L::o_wy, i - kBW);
-                    wgt[3] = ldc(s0, L::o_wy, i);
-                    wgt[4] = wzm1[k];
-                    wgt[5] = wzp;
-                    val = P::sweep_of(nb, wgt, ldc(s0, L::o_id, i), fi, uc1[k], om1);
-                } else {
-                    val = P::sweep_const(nb, cconst, invd_c, fi, uc1[k], om1);
-                }
-            }
-            l1z[tid + kT2Threads * k] = val;
-            um1[k] = uc1[k];
-            uc1[k] = up;
-            if constexpr (VARK) wzm1[k] = wzp;
-        }
-        __syncthreads();
-        // level 2: plane z - 1 of the tile, from level-1 planes z - 2 (carried),
-        // z - 1 (ring: neighbours, carried: centre) and z (ring)
-        const T *l1m = l1(z - 1);
+            const V up = ld_u2(sp, ix, 0);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const T vp = l1z[li2[q]];
-            if (z - 1 >= z0 && in2[q]) {
-                T nb[6];
-                nb[0] = l1m[li2[q] - 1];
-                nb[1] = l1m[li2[q] + 1];
-                nb[2] = l1m[li2[q] - kL1W];
-                nb[3] = l1m[li2[q] + kL1W];
-                nb[4] = vm2[q];
-                nb[5] = vp;
-                T un;
-                if constexpr (VARK) {
-                    C wgt[6] = {cwxm[q], cwxp[q], cwym[q], cwyp[q], cwzm[q], cwzp[q]};
-                    un = P::sweep_of(nb, wgt, cid[q], cf[q], vc2[q], om2);
-                } else {
-                    un = P::sweep_const(nb, cconst, invd_c, cf[q], vc2[q], om2);
-                }
-                store_u<PREC>(a.bufs, dst, col2[q] + (long long)g.plane * (z - 1), un);
-            }
-            vm2[q] = vc2[q];
-            vc2[q] = vp;
-            // the coefficients of plane z, for the next step
-            const int i = si2[q];
-            cf[q] = ldc(s0, L::o_f, i);
+            for (int j = 1; j < 8; ++j) nc[j] = wzero2();
+            nc[0] = ld_c2(s0, L::o_f, ix, 0);
             if constexpr (VARK) {
-                cwxm[q] = ldc(s0, L::o_wx, i - 1);
-                cwxp[q] = ldc(s0, L::o_wx, i);
-                cwym[q] = ldc(s0, L::o_wy, i - kBW);
-                cwyp[q] = ldc(s0, L::o_wy, i);
-                cwzm[q] = cwzp[q];
-                cwzp[q] = ldc(s0, L::o_wz, i);
-                cid[q] = ldc(s0, L::o_id, i);
+                nc[1] = ld_c2(s0, L::o_wx, ix, -1);
+                nc[2] = ld_c2(s0, L::o_wx, ix, 0);
+                nc[3] = ld_c2(s0, L::o_wy, ix, -kBW);
+                nc[4] = ld_c2(s0, L::o_wy, ix, 0);
+                nc[5] = wzm;
+                nc[6] = ld_c2(s0, L::o_wz, ix, 0);
+                nc[7] = ld_c2(s0, L::o_id, ix, 0);
             }
+            V val = zero2();
+            if (zin && (k[0] || k[1])) {
+                const V nb[6] = {ld_u2(s0, ix, -1), ld_u2(s0, ix, 1), ld_u2(s0, ix, -kBW),
+                                 ld_u2(s0, ix, kBW), um, up};
+                val = keep(sweep2(nb, nc + 1, nc[7], nc[0], uc, om1, om1f), k[0], k[1]);
+            }
+            S::st1(l1z, jx[0], get(val, 0));
+            S::st1(l1z, jx[1], get(val, 1));
+            um = uc;
+            uc = up;
+            if constexpr (VARK) wzm = nc[6];
+            return val;
+        };
+        // the thread's tile points; level 2 takes the coefficients read here
+        // one step later
+        W nc[8];  // f, faces -x +x -y +y -z +z, 1/D of plane z
+        const V val = level1(si, li, in, um1, uc1, wzm1, nc);
+        // level 2: plane z - 1 of the thread's two points, from level-1 planes
+        // z - 2 (carried), z - 1 (ring: neighbours, carried: centre) and z
+        // (this step's level-1 value), with the coefficients level 1 read for
+        // plane z - 1.  Plane z - 1 of the level-1 ring was complete at the
+        // barrier that opened this step, and nothing writes it during the
+        // step (level 1 writes plane z, the other half of the ring), so no
+        // barrier separates the levels.
+        if (z - 1 >= z0 && (in[0] || in[1])) {
+            const unsigned char *l1m = l1(z - 1);
+            const V nb[6] = {ld_l1(l1m, -1), ld_l1(l1m, 1), ld_l1(l1m, -kL1W), ld_l1(l1m, kL1W),
+                             vm2, val};
+            const V un = sweep2(nb, cw + 1, cw[7], cw[0], vc2, om2, om2f);
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (in[q]) store_u<PREC>(a.bufs, dst, col[q] + (long long)g.plane * (z - 1), get(un, q));
+        }
+        vm2 = vc2;
+        vc2 = val;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cw[j] = nc[j];
+        // level 1 on the ring pair (threads 0 .. 49); level 2 reads it from
+        // the next step on
+        if (hasH) {
+            W ncH[8];
+            level1(siH, liH, inH, um1H, uc1H, wzm1H, ncH);
         }
     }
     // every copy in flight lands before the shared memory goes away (the
