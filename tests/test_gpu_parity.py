@@ -633,6 +633,42 @@ def test_plane3d_two_sweeps_mixed_solve(S, orc, name, n, kind, depth):
     assert np.linalg.norm(ug - ref["u"]) <= (rn_true + ref["rn"]) / lam * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("name,n,kind", P3D2_CASES, ids=[c[0] for c in P3D2_CASES])
+def test_plane3d_two_sweeps_bitwise_equal_one_sweep_passes(S, name, n, kind):
+    """The two-sweep pass performs, per point, the operations of the one-sweep
+    pass in the same order (the FP32-pair form on packed pairs, each component
+    rounded as the scalar form), so a temporal depth of 2 changes the number
+    of passes and nothing else: the FP64 iterates of a fixed schedule and the
+    mixed-precision solve (sweeps, cycles, final levels, solution) are
+    bit-identical to those of depth 1."""
+    f = inputs.uniform_rhs(n, seed=54).ravel()
+    k = inputs.lognormal_k(n, seed=3, corr=4.0) if kind else None
+    eps = [1.0, 0.7, 1.3] if kind else None
+    levels = [0, 1, 2, 3, 4, 5, 8, 11, 9, 12]
+    out = {}
+    for depth in (1, 2):
+        h, kt = make(S, n, S.SRJ_PREC_F64, eps=eps, k=k, temporal_depth=depth)
+        fd, ud = dev(f), dev(np.zeros(f.size))
+        try:
+            rn = S.srj_run_levels(h, fd.data_ptr(), ud.data_ptr(), levels)
+            u64 = ud.cpu().numpy()
+        finally:
+            S.srj_destroy(h)
+        h, kt = make(S, n, S.SRJ_PREC_MIXED, eps=eps, k=k, temporal_depth=depth)
+        fd, ud = dev(f), dev(np.zeros(f.size))
+        try:
+            st = S.srj_solve(h, fd.data_ptr(), ud.data_ptr(), 1e-8)
+            umx = ud.cpu().numpy()
+        finally:
+            S.srj_destroy(h)
+        out[depth] = (u64, np.asarray(rn), umx, st)
+    np.testing.assert_array_equal(out[1][0], out[2][0])
+    np.testing.assert_array_equal(out[1][1], out[2][1])
+    np.testing.assert_array_equal(out[1][2], out[2][2])
+    for key in ("status", "sweeps", "cycles", "outer", "final_level", "rn"):
+        assert out[1][3][key] == out[2][3][key], key
+
+
 @pytest.mark.parametrize("name,n,kind", P3D2_CASES[:2], ids=[c[0] for c in P3D2_CASES[:2]])
 def test_plane3d_two_sweeps_f32_within_bound(S, orc, name, n, kind):
     f = inputs.uniform_rhs(n, seed=53).ravel()
