@@ -144,7 +144,8 @@ typedef struct srj_opts {
     int32_t temporal_depth; /* sweeps fused per HBM pass; 0 = library choice.
                                2D constant coefficients: 1 or 2 (F64), 4 or 8
                                (F32), 2 or 4 (MIXED); 3D Dirichlet: 1 or 2
-                               (default 2 for MIXED, 1 otherwise) */
+                               (default 2 for MIXED, 1 otherwise; the 3D
+                               iterates are the same bit for bit at 1 and 2) */
     int32_t trace_capacity; /* per-cycle records kept (0 means 4096) */
     int64_t max_sweeps;     /* sweep cap per solve (0 means 1000000) */
     double inner_tol;       /* SRJ_PREC_MIXED: floor of the inner solves' relative
